@@ -1,0 +1,197 @@
+/*
+ * empc.h - C ABI of the GB300 evolutionary-MPC (EMPC) library.
+ *
+ * One generation of EMPC, after Hyatt, Williams & Killpack, "Parameterized
+ * and GPU-Parallelized Real-Time Model Predictive Control for High Degree of
+ * Freedom Robots" (arXiv 2001.04931), Sec. V and Algorithm 1:
+ *   breed (cold start: uniform in the input bounds; warm start: two parents
+ *   drawn from the elites, uniform crossover, Gaussian mutation, clip),
+ *   expand the knots into per-step inputs (Sec. IV-C), roll the discrete
+ *   linear model forward (Eq. first_order_integration), accumulate the
+ *   quadratic cost (Eq. mpc_problem), keep the E best (elitism).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major.  Host inputs are FP64 and copied at call time;
+ *    the caller keeps ownership of every buffer it passes.
+ *  - "dev" pointers are CUDA device pointers on the handle's device; "host"
+ *    pointers are ordinary host memory.  Device-pointer calls are
+ *    asynchronous on the handle's stream; host-pointer calls return after the
+ *    results are in the caller's buffers.
+ *  - The population is SoA FP32: parameter q = i*p + j (input i, knot j) of
+ *    candidate c is pop[q*P + c].
+ *  - Every call returns an empc_status; nothing throws across the ABI.  On
+ *    failure empc_last_error(h) (or empc_last_error(NULL) for calls without
+ *    a handle) describes the cause.
+ *  - A handle is not thread-safe: one host thread at a time.
+ *  - There is no CPU fallback: without a usable CUDA device, calls that need
+ *    one fail with EMPC_ECUDA.
+ */
+#ifndef EMPC_H
+#define EMPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct empc_problem_s* empc_handle;
+
+typedef enum {
+    EMPC_OK = 0,
+    EMPC_EINVAL = 1,       /* bad argument (null pointer, size, bound, non-finite input) */
+    EMPC_ENOMEM = 2,       /* device or pinned host allocation failed */
+    EMPC_ECUDA = 3,        /* CUDA runtime error (no device, launch failure, ...) */
+    EMPC_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+    EMPC_ENONFINITE = 5,   /* the best cost is +inf or NaN (unstable model or inputs) */
+    EMPC_ESTATE = 6,       /* call not valid in the handle's state */
+    EMPC_EUNSUPPORTED = 7  /* valid request outside what the GPU path implements */
+} empc_status;
+
+typedef enum { EMPC_FP32 = 0, EMPC_BF16 = 1 } empc_precision;
+
+/* Granularity of the 50% mutation decision (Sec. V: "each input has a 50%
+ * probability of being mutated"; Algorithm 1 adds the noise unconditionally). */
+typedef enum {
+    EMPC_GATE_PER_INPUT = 0, /* one decision per (child, input); all its knots move together */
+    EMPC_GATE_PER_KNOT = 1,  /* one decision per (child, knot parameter) */
+    EMPC_GATE_ALWAYS = 2     /* every parameter mutated (Algorithm 1 read literally) */
+} empc_gate;
+
+typedef struct {
+    uint64_t seed;       /* Philox4x32-10 key (lo, hi words) */
+    int elite;           /* numParents E; 0 = max(1, P/16) */
+    float sigma;         /* sigma_noise of the mutation, default 0.1 */
+    int p_cross_256;     /* P(take parameter from parent 2) * 256, default 128 */
+    int p_mutate_256;    /* P(mutate) * 256, default 128 */
+    int gate;            /* empc_gate, default EMPC_GATE_PER_INPUT */
+    int precision;       /* empc_precision, default EMPC_FP32 */
+    int refine_steps;    /* projected-gradient steps on the elites per generation, default 0 */
+    float refine_lr;     /* step size; 0 = 1/L, L the gradient's Lipschitz constant */
+    int ckpt_every;      /* adjoint checkpoint interval; 0 = ceil(sqrt(T)) */
+    int tile;            /* 0 = autotune the rollout tile; k > 0 forces candidate shape k-1 */
+} empc_config;
+
+typedef struct {
+    int n, m, horizon, knots, pop, elite;
+    uint64_t generation;     /* generations run so far (keys the next draws) */
+    int tile_nx, tile_rows, tile_cands, tile_groups; /* rollout tile chosen */
+    int threads_per_cta, smem_bytes, ctas;
+    float tuned_us;          /* autotuner's best rollout time (microseconds), 0 if forced */
+    float refine_lr;         /* projected-gradient step in use */
+    int tile_kind;           /* 0: block-synchronous rollout, 1: warp-synchronous */
+} empc_info;
+
+/* Defaults listed in empc_config. */
+void empc_config_default(empc_config* cfg);
+
+/*
+ * empc_create - build a problem on the current CUDA device.
+ *   A [n*n], B [n*m]  discrete model x_{k+1} = A x_k + B u_k (Eq.
+ *                     first_order_integration, w_d = 0); host FP64.
+ *   Q [n*n], R [m*m]  cost weights of Eq. mpc_problem (u_goal = 0); host FP64.
+ *                     Must be diagonal with non-negative entries (else
+ *                     EMPC_EUNSUPPORTED / EMPC_EINVAL).
+ *   bounds [m*2]      (u_min, u_max) per input; knots are clipped to them.
+ *   horizon T >= 1, knots p in [1, T] (Sec. IV-C), pop P >= 1, n <= 128.
+ *   cfg               NULL for defaults.
+ * The cost of a knot vector U is
+ *   J(U) = sum_{k=0}^{T-1} (x_{k+1}-g)' Q (x_{k+1}-g) + u_k' R u_k,
+ * the stage cost taken after each update as Algorithm 1 accumulates it.
+ * Allocates all device memory the handle needs; *out receives the handle.
+ */
+empc_status empc_create(const double* A, const double* B, const double* Q, const double* R,
+                        const double* bounds, int n, int m, int horizon, int knots, int pop,
+                        const empc_config* cfg, empc_handle* out);
+
+/*
+ * empc_solve - run `generations` >= 1 generations of Algorithm 1 from host
+ * x0 [n] and x_goal [n] (FP64).  The population persists across calls (warm
+ * start, Sec. V); the first call after create or empc_reset starts cold.
+ * Writes the best knot vector (host, [m*p], parameter q = i*p + j) and its
+ * cost.  u* of Algorithm 1 is best_knots[i*p + 0] for each input i.
+ * Host-to-device copy of x0/x_goal, the generations, and the device-to-host
+ * copy of the result all happen inside the call (the paper's EMPC solve time,
+ * Sec. VI-A).  Returns EMPC_ENONFINITE if the best cost is not finite.
+ */
+empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal,
+                       int generations, float* best_knots, float* best_cost);
+
+/*
+ * empc_solve_device - as empc_solve with device inputs and outputs:
+ * dev_x0 [n], dev_goal [n] (FP32), dev_best_knots [m*p], dev_best_cost [1].
+ * Asynchronous on the handle's stream; no host synchronization.
+ */
+empc_status empc_solve_device(empc_handle h, const float* dev_x0, const float* dev_goal,
+                              int generations, float* dev_best_knots, float* dev_best_cost);
+
+/*
+ * empc_evaluate - costs of a given population (no breeding): the rollout and
+ * cost of Algorithm 1 applied to dev_pop [m*p][count] (SoA with stride
+ * `count`), writing dev_cost [count].  Asynchronous.
+ */
+empc_status empc_evaluate(empc_handle h, const float* dev_x0, const float* dev_goal,
+                          const float* dev_pop, int count, float* dev_cost);
+
+/*
+ * empc_get_state - copy the current population [m*p][P], its costs [P] and
+ * the elite indices [E] in rank order (best first) to device buffers; any
+ * pointer may be NULL.  Asynchronous.  EMPC_ESTATE before the first solve.
+ */
+empc_status empc_get_state(empc_handle h, float* dev_pop, float* dev_cost, int* dev_elite);
+
+/*
+ * empc_set_state - replace the population, costs and elite indices (all
+ * three device buffers required); the next generation breeds from them.
+ */
+empc_status empc_set_state(empc_handle h, const float* dev_pop, const float* dev_cost,
+                           const int* dev_elite);
+
+/* empc_reset - the next generation is a cold start.  The generation counter
+ * keeps counting, so draws never repeat within a handle. */
+empc_status empc_reset(empc_handle h);
+
+/* empc_set_stream - run subsequent work on `stream` (a cudaStream_t); NULL
+ * selects the handle's own stream. */
+empc_status empc_set_stream(empc_handle h, void* stream);
+
+empc_status empc_get_info(empc_handle h, empc_info* info);
+
+/*
+ * empc_time_generation - measurement aid (no counterpart in the paper): run
+ * `reps` warm generations as plain launches on the handle's stream and
+ * report the average duration of the fused breed+rollout+cost kernel and of
+ * the elite-selection kernel, from CUDA events around each launch.  The
+ * generations are real (the population advances).  EMPC_ESTATE before the
+ * first solve.  Synchronizes the stream.
+ */
+empc_status empc_time_generation(empc_handle h, int reps, float* rollout_us, float* select_us);
+
+/*
+ * empc_measure_fp32_peak - measurement aid (no counterpart in the paper):
+ * FP32 fused-multiply-add throughput of the current device in TFLOP/s (2
+ * flops per FMA) from a register-only kernel, best of 5 timed launches.
+ */
+empc_status empc_measure_fp32_peak(double* tflops);
+
+/* empc_destroy - free the handle and its device memory (NULL is a no-op). */
+void empc_destroy(empc_handle h);
+
+/* empc_last_error - text of the last failure on h (or of the calling thread
+ * for calls without a handle when h is NULL).  Owned by the library. */
+const char* empc_last_error(empc_handle h);
+
+/*
+ * empc_discretize_zoh - zero-order-hold discretization of x' = Ac x + Bc u
+ * over dt (Sec. III-A, "matrix exponential"): [[Ad, Bd], [0, I]] =
+ * expm([[Ac, Bc], [0, 0]] dt).  Host FP64, row-major; Ad [n*n], Bd [n*m]
+ * are caller-owned outputs.  Needs no GPU.
+ */
+empc_status empc_discretize_zoh(const double* Ac, const double* Bc, int n, int m, double dt,
+                                double* Ad, double* Bd);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMPC_H */

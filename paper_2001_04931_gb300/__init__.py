@@ -1,0 +1,217 @@
+"""Python binding of the EMPC C-ABI library (libempc.so, include/empc.h).
+
+Argument marshalling only: every step of an EMPC generation (breeding, knot
+expansion, rollout, cost, elite selection) runs in the library's CUDA
+kernels.  The raw entry points carry the C names (empc_create, empc_solve,
+...); `Problem` wraps a handle for numpy / torch callers.  PyTorch is used
+only to own device memory and streams.
+
+Importing this module raises if the compiled library is missing: there is no
+CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libempc.so")
+
+EMPC_OK, EMPC_EINVAL, EMPC_ENOMEM, EMPC_ECUDA, EMPC_ETIMEOUT = 0, 1, 2, 3, 4
+EMPC_ENONFINITE, EMPC_ESTATE, EMPC_EUNSUPPORTED = 5, 6, 7
+EMPC_FP32, EMPC_BF16 = 0, 1
+EMPC_GATE_PER_INPUT, EMPC_GATE_PER_KNOT, EMPC_GATE_ALWAYS = 0, 1, 2
+
+_STATUS = {0: "EMPC_OK", 1: "EMPC_EINVAL", 2: "EMPC_ENOMEM", 3: "EMPC_ECUDA",
+           4: "EMPC_ETIMEOUT", 5: "EMPC_ENONFINITE", 6: "EMPC_ESTATE",
+           7: "EMPC_EUNSUPPORTED"}
+
+
+class empc_config(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("elite", ctypes.c_int), ("sigma", ctypes.c_float),
+                ("p_cross_256", ctypes.c_int), ("p_mutate_256", ctypes.c_int),
+                ("gate", ctypes.c_int), ("precision", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("refine_lr", ctypes.c_float),
+                ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int)]
+
+
+class empc_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("horizon", ctypes.c_int),
+                ("knots", ctypes.c_int), ("pop", ctypes.c_int), ("elite", ctypes.c_int),
+                ("generation", ctypes.c_uint64), ("tile_nx", ctypes.c_int),
+                ("tile_rows", ctypes.c_int), ("tile_cands", ctypes.c_int),
+                ("tile_groups", ctypes.c_int), ("threads_per_cta", ctypes.c_int),
+                ("smem_bytes", ctypes.c_int), ("ctas", ctypes.c_int),
+                ("tuned_us", ctypes.c_float), ("refine_lr", ctypes.c_float),
+                ("tile_kind", ctypes.c_int)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+_h = ctypes.c_void_p
+_i = ctypes.c_int
+
+# name -> (restype, argtypes); the C declarations are in include/empc.h
+_SIGNATURES = {
+    "empc_config_default": (None, [ctypes.POINTER(empc_config)]),
+    "empc_create": (_i, [_dp, _dp, _dp, _dp, _dp, _i, _i, _i, _i, _i,
+                         ctypes.POINTER(empc_config), ctypes.POINTER(_h)]),
+    "empc_solve": (_i, [_h, _dp, _dp, _i, _fp, _fp]),
+    "empc_solve_device": (_i, [_h, _vp, _vp, _i, _vp, _vp]),
+    "empc_evaluate": (_i, [_h, _vp, _vp, _vp, _i, _vp]),
+    "empc_get_state": (_i, [_h, _vp, _vp, _vp]),
+    "empc_set_state": (_i, [_h, _vp, _vp, _vp]),
+    "empc_reset": (_i, [_h]),
+    "empc_set_stream": (_i, [_h, _vp]),
+    "empc_get_info": (_i, [_h, ctypes.POINTER(empc_info)]),
+    "empc_destroy": (None, [_h]),
+    "empc_last_error": (ctypes.c_char_p, [_h]),
+    "empc_discretize_zoh": (_i, [_dp, _dp, _i, _i, ctypes.c_double, _dp, _dp]),
+    "empc_time_generation": (_i, [_h, _i, _fp, _fp]),
+    "empc_measure_fp32_peak": (_i, [_dp]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python paper_2001_04931_gb300/build.py` "
+            "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+_lib = _load()
+globals().update({name: getattr(_lib, name) for name in _SIGNATURES})
+
+
+class EmpcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, handle=None):
+    if status != EMPC_OK:
+        msg = _lib.empc_last_error(handle)
+        raise EmpcError(status, msg.decode() if msg else "")
+    return status
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _dev(t):
+    """Device pointer of a CUDA tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return t.data_ptr()
+
+
+def default_config(**kw):
+    cfg = empc_config()
+    _lib.empc_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def discretize_zoh(Ac, Bc, dt):
+    """Zero-order-hold (Ad, Bd) of x' = Ac x + Bc u over dt (host, FP64)."""
+    Ac, Bc = _d(Ac), _d(Bc)
+    n, m = Bc.shape
+    Ad, Bd = np.zeros((n, n)), np.zeros((n, m))
+    check(_lib.empc_discretize_zoh(_ptr(Ac), _ptr(Bc), n, m, float(dt), _ptr(Ad), _ptr(Bd)))
+    return Ad, Bd
+
+
+def measure_fp32_peak():
+    """Measured FP32 FMA throughput of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    check(_lib.empc_measure_fp32_peak(ctypes.byref(v)))
+    return v.value
+
+
+class Problem:
+    """One EMPC problem on the current CUDA device (owns an empc_handle)."""
+
+    def __init__(self, A, B, Q, R, bounds, horizon, knots, pop, config=None, **cfg):
+        A, B, Q, R, bounds = _d(A), _d(B), _d(Q), _d(R), _d(bounds)
+        self.n, self.m = B.shape
+        self.T, self.p, self.P = int(horizon), int(knots), int(pop)
+        self.D = self.m * self.p
+        c = config if config is not None else default_config(**cfg)
+        h = _h()
+        check(_lib.empc_create(_ptr(A), _ptr(B), _ptr(Q), _ptr(R), _ptr(bounds), self.n,
+                               self.m, self.T, self.p, self.P, ctypes.byref(c),
+                               ctypes.byref(h)))
+        self.handle = h
+        self.E = self.info().elite
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.empc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = empc_info()
+        check(_lib.empc_get_info(self.handle, ctypes.byref(inf)), self.handle)
+        return inf
+
+    def solve(self, x0, x_goal, generations):
+        """Host in, host out: (best_knots[m*p] float32, best_cost float)."""
+        x0, g = _d(x0), _d(x_goal)
+        out = np.zeros(self.D, np.float32)
+        cost = ctypes.c_float()
+        check(_lib.empc_solve(self.handle, _ptr(x0), _ptr(g), int(generations),
+                              out.ctypes.data_as(_fp), ctypes.byref(cost)), self.handle)
+        return out, cost.value
+
+    def solve_device(self, x0, x_goal, generations, best_knots, best_cost):
+        check(_lib.empc_solve_device(self.handle, _dev(x0), _dev(x_goal), int(generations),
+                                     _dev(best_knots), _dev(best_cost)), self.handle)
+
+    def evaluate(self, x0, x_goal, pop, cost):
+        """Costs of pop [m*p, count] (CUDA tensors) into cost [count]."""
+        check(_lib.empc_evaluate(self.handle, _dev(x0), _dev(x_goal), _dev(pop),
+                                 int(pop.shape[1]), _dev(cost)), self.handle)
+
+    def get_state(self, pop=None, cost=None, elite=None):
+        check(_lib.empc_get_state(self.handle, _dev(pop), _dev(cost), _dev(elite)),
+              self.handle)
+
+    def set_state(self, pop, cost, elite):
+        check(_lib.empc_set_state(self.handle, _dev(pop), _dev(cost), _dev(elite)),
+              self.handle)
+
+    def reset(self):
+        check(_lib.empc_reset(self.handle), self.handle)
+
+    def time_generation(self, reps):
+        """Average (rollout_us, select_us) of `reps` warm generations."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        check(_lib.empc_time_generation(self.handle, int(reps), ctypes.byref(a),
+                                        ctypes.byref(b)), self.handle)
+        return a.value, b.value
+
+    def set_stream(self, stream):
+        check(_lib.empc_set_stream(self.handle, stream), self.handle)

@@ -1,0 +1,733 @@
+// Host side of the EMPC C ABI (include/empc.h): validation, model staging,
+// device buffers, the per-generation launch sequence, CUDA-graph capture of a
+// whole solve, and the rollout-tile autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/empc.h"
+#include "empc_internal.h"
+
+using empc::KnotStep;
+using empc::RolloutArgs;
+using empc::TileShape;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+struct GraphKey {
+    int generations;
+    int cold_first;
+    int parity;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(generations, cold_first, parity) <
+               std::tie(o.generations, o.cold_first, o.parity);
+    }
+};
+
+}  // namespace
+
+struct empc_problem_s {
+    int n = 0, m = 0, T = 0, p = 0, P = 0, E = 0, D = 0;
+    empc_config cfg{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    // model, FP32 on device
+    float *D_ = nullptr, *BT = nullptr, *qdiag = nullptr, *rdiag = nullptr, *gram = nullptr;
+    float *umin = nullptr, *umax = nullptr, *x0 = nullptr, *goal = nullptr;
+    KnotStep* ktab = nullptr;
+    // population state
+    float* pop[2] = {nullptr, nullptr};
+    float* cost = nullptr;
+    int* elite_idx = nullptr;
+    float* elite_cost = nullptr;
+    float* best_knots = nullptr;
+    float* best_cost = nullptr;
+    uint32_t* gen = nullptr;
+    int* status = nullptr;
+    // pinned staging: x0, goal (2n) | best knots (D) | best cost | status
+    float* stage = nullptr;
+    int cur = 0;
+    bool has_pop = false;
+    uint64_t gen_host = 0;
+    TileShape shape{};
+    float tuned_us = 0.0f;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::string err;
+};
+
+namespace {
+
+empc_status fail(empc_handle h, empc_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    g_thread_error = msg;
+    return s;
+}
+
+empc_status cuda_fail(empc_handle h, cudaError_t e, const char* where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                      cudaGetErrorString(e) + ")";
+    return fail(h, EMPC_ECUDA, msg);
+}
+
+#define EMPC_CUDA(h, call)                                          \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+    } while (0)
+
+bool finite_all(const double* v, size_t k) {
+    for (size_t i = 0; i < k; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// Knot table of Sec. IV-C in exact integers: idx1 = min(floor(k (p-1) /
+// (T-1)), p-2), c = (k (p-1) - idx1 (T-1)) / (T-1).  The weights are exact
+// rationals rounded once to FP32.  p == 1 or T == 1: constant input.
+void make_knot_table(int T, int p, std::vector<KnotStep>& ks, std::vector<double>& w0,
+                     std::vector<double>& w1, std::vector<int>& idx) {
+    ks.resize(T);
+    w0.resize(T);
+    w1.resize(T);
+    idx.resize(T);
+    const long den = T > 1 ? T - 1 : 1;
+    for (int k = 0; k < T; ++k) {
+        long a = 0, num = 0;
+        if (p > 1 && T > 1) {
+            a = std::min<long>((long)k * (p - 1) / den, p - 2);
+            num = (long)k * (p - 1) - a * den;
+        }
+        idx[k] = (int)a;
+        w1[k] = (double)num / (double)den;
+        w0[k] = (double)(den - num) / (double)den;
+        ks[k].idx1 = (int)a;
+        ks[k].w0 = (float)w0[k];
+        ks[k].w1 = (float)w1[k];
+        ks[k].pad = 0;
+    }
+}
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+}
+
+RolloutArgs base_args(empc_handle h) {
+    RolloutArgs a{};
+    a.D = h->D_;
+    a.BT = h->BT;
+    a.qdiag = h->qdiag;
+    a.rdiag = h->rdiag;
+    a.gram = h->gram;
+    a.ktab = h->ktab;
+    a.x0 = h->x0;
+    a.goal = h->goal;
+    a.umin = h->umin;
+    a.umax = h->umax;
+    a.n = h->n;
+    a.m = h->m;
+    a.T = h->T;
+    a.p = h->p;
+    a.P = h->P;
+    a.E = h->E;
+    a.seed = h->cfg.seed;
+    a.gen = h->gen;
+    a.sigma = h->cfg.sigma;
+    a.pc256 = h->cfg.p_cross_256;
+    a.pm256 = h->cfg.p_mutate_256;
+    a.gate = h->cfg.gate;
+    return a;
+}
+
+// One generation: breed (cold or warm) + rollout + cost into pop[parity^1],
+// then elite selection.
+cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_t st) {
+    RolloutArgs a = base_args(h);
+    a.mode = cold ? empc::kCold : empc::kWarm;
+    a.pop_in = h->pop[parity];
+    a.pop_out = h->pop[parity ^ 1];
+    a.cost = h->cost;
+    a.elite_idx = h->elite_idx;
+    cudaError_t e = empc::launch_rollout(a, h->shape, st);
+    if (e != cudaSuccess) return e;
+    return empc::launch_select(h->cost, h->P, h->E, h->pop[parity ^ 1], h->D, h->elite_idx,
+                               h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
+                               st);
+}
+
+empc_status run_generations(empc_handle h, int G) {
+    const GraphKey key{G, h->has_pop ? 0 : 1, h->cur};
+    auto it = h->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it != h->graphs.end()) {
+        exec = it->second;
+    } else {
+        cudaStream_t cap = h->own_stream;
+        EMPC_CUDA(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        bool cold = !h->has_pop;
+        int parity = h->cur;
+        cudaError_t e = cudaSuccess;
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            e = enqueue_generation(h, cold, parity, cap);
+            cold = false;
+            parity ^= 1;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(h, e, "enqueue_generation (capture)");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        h->graphs[key] = exec;
+    }
+    EMPC_CUDA(h, cudaGraphLaunch(exec, h->stream));
+    h->cur ^= (G & 1);
+    h->has_pop = true;
+    h->gen_host += (uint64_t)G;
+    return EMPC_OK;
+}
+
+empc_status autotune(empc_handle h) {
+    TileShape buf[128];
+    const int ns = std::min(empc::rollout_shapes(h->n, buf, 128), 128);
+    std::vector<TileShape> shapes(buf, buf + ns);
+    std::vector<TileShape> ok;
+    for (const TileShape& s : shapes)
+        if (empc::rollout_shape_supported(s, h->n, h->m, h->p, h->T)) ok.push_back(s);
+    if (ok.empty()) return fail(h, EMPC_EUNSUPPORTED, "no rollout tile fits this problem");
+    // score a cold-start population of the real size
+    RolloutArgs a = base_args(h);
+    a.mode = empc::kCold;
+    a.pop_out = h->pop[0];
+    a.cost = h->cost;
+    a.gen = nullptr;
+    if (h->cfg.tile > 0) {
+        const size_t k = (size_t)(h->cfg.tile - 1);
+        if (k >= ok.size()) return fail(h, EMPC_EINVAL, "cfg.tile out of range");
+        h->shape = ok[k];
+        // one launch outside any capture sets the kernel's shared-memory cap
+        EMPC_CUDA(h, empc::launch_rollout(a, h->shape, h->stream));
+        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+        return EMPC_OK;
+    }
+    cudaEvent_t e0, e1;
+    EMPC_CUDA(h, cudaEventCreate(&e0));
+    EMPC_CUDA(h, cudaEventCreate(&e1));
+    float best = 1e30f;
+    TileShape best_s = ok[0];
+    for (const TileShape& s : ok) {
+        if (empc::launch_rollout(a, s, h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float t_min = 1e30f;
+        bool good = true;
+        for (int rep = 0; rep < 3 && good; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            good = empc::launch_rollout(a, s, h->stream) == cudaSuccess;
+            cudaEventRecord(e1, h->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) good = false;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_min = std::min(t_min, ms);
+        }
+        if (!good) {
+            cudaGetLastError();
+            continue;
+        }
+        if (t_min < best) {
+            best = t_min;
+            best_s = s;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->shape = best_s;
+    h->tuned_us = best * 1000.0f;
+    return EMPC_OK;
+}
+
+void free_handle(empc_handle h) {
+    if (!h) return;
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    void* bufs[] = {h->D_, h->BT, h->qdiag, h->rdiag, h->gram, h->umin, h->umax, h->x0,
+                    h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
+                    h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->stage) cudaFreeHost(h->stage);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+// ---------------------------------------------------------------------------
+// Zero-order hold by the matrix exponential: scaling and squaring with the
+// diagonal [6/6] Pade approximant (Moler & Van Loan, "Nineteen dubious ways
+// to compute the exponential of a matrix", method 3).
+// ---------------------------------------------------------------------------
+void mat_mul(const std::vector<double>& X, const std::vector<double>& Y,
+             std::vector<double>& Z, int N) {
+    std::vector<double> out((size_t)N * N, 0.0);
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < N; ++k) {
+            const double x = X[(size_t)i * N + k];
+            if (x == 0.0) continue;
+            for (int j = 0; j < N; ++j) out[(size_t)i * N + j] += x * Y[(size_t)k * N + j];
+        }
+    Z.swap(out);
+}
+
+bool solve_in_place(std::vector<double> M, std::vector<double>& Bm, int N) {
+    // Gaussian elimination with partial pivoting: M X = Bm, X overwrites Bm.
+    for (int col = 0; col < N; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < N; ++r)
+            if (std::fabs(M[(size_t)r * N + col]) > std::fabs(M[(size_t)piv * N + col])) piv = r;
+        if (M[(size_t)piv * N + col] == 0.0) return false;
+        if (piv != col)
+            for (int j = 0; j < N; ++j) {
+                std::swap(M[(size_t)piv * N + j], M[(size_t)col * N + j]);
+                std::swap(Bm[(size_t)piv * N + j], Bm[(size_t)col * N + j]);
+            }
+        const double inv = 1.0 / M[(size_t)col * N + col];
+        for (int r = 0; r < N; ++r) {
+            if (r == col) continue;
+            const double f = M[(size_t)r * N + col] * inv;
+            if (f == 0.0) continue;
+            for (int j = 0; j < N; ++j) {
+                M[(size_t)r * N + j] -= f * M[(size_t)col * N + j];
+                Bm[(size_t)r * N + j] -= f * Bm[(size_t)col * N + j];
+            }
+        }
+    }
+    for (int r = 0; r < N; ++r) {
+        const double inv = 1.0 / M[(size_t)r * N + r];
+        for (int j = 0; j < N; ++j) Bm[(size_t)r * N + j] *= inv;
+    }
+    return true;
+}
+
+bool expm_pade6(const std::vector<double>& A, int N, std::vector<double>& out) {
+    double norm = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < N; ++j) s += std::fabs(A[(size_t)i * N + j]);
+        norm = std::max(norm, s);
+    }
+    int sq = 0;
+    if (norm > 0.5) sq = (int)std::ceil(std::log2(norm / 0.5));
+    const double scale = std::ldexp(1.0, -sq);
+    std::vector<double> X(A);
+    for (double& v : X) v *= scale;
+    // N_6(X) = sum c_k X^k, D_6(X) = sum (-1)^k c_k X^k,
+    // c_k = (2q-k)! q! / ((2q)! k! (q-k)!), q = 6.
+    const int q = 6;
+    std::vector<double> c(q + 1);
+    c[0] = 1.0;
+    for (int k = 1; k <= q; ++k) c[k] = c[k - 1] * (double)(q - k + 1) / (double)(k * (2 * q - k + 1));
+    std::vector<double> Np((size_t)N * N, 0.0), Dp((size_t)N * N, 0.0), Pk((size_t)N * N, 0.0);
+    for (int i = 0; i < N; ++i) Pk[(size_t)i * N + i] = 1.0;
+    for (int k = 0; k <= q; ++k) {
+        if (k > 0) mat_mul(Pk, X, Pk, N);
+        const double sgn = (k & 1) ? -1.0 : 1.0;
+        for (size_t t = 0; t < Pk.size(); ++t) {
+            Np[t] += c[k] * Pk[t];
+            Dp[t] += sgn * c[k] * Pk[t];
+        }
+    }
+    if (!solve_in_place(Dp, Np, N)) return false;
+    for (int s = 0; s < sq; ++s) mat_mul(Np, Np, Np, N);
+    out.swap(Np);
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void empc_config_default(empc_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->seed = 0x5EEDull;
+    cfg->elite = 0;
+    cfg->sigma = 0.1f;
+    cfg->p_cross_256 = 128;
+    cfg->p_mutate_256 = 128;
+    cfg->gate = EMPC_GATE_PER_INPUT;
+    cfg->precision = EMPC_FP32;
+    cfg->refine_steps = 0;
+    cfg->refine_lr = 0.0f;
+    cfg->ckpt_every = 0;
+    cfg->tile = 0;
+}
+
+empc_status empc_create(const double* A, const double* B, const double* Q, const double* R,
+                        const double* bounds, int n, int m, int horizon, int knots, int pop,
+                        const empc_config* cfg_in, empc_handle* out) {
+    if (!out) return fail(nullptr, EMPC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!A || !B || !Q || !R || !bounds) return fail(nullptr, EMPC_EINVAL, "NULL model pointer");
+    if (n < 1 || n > 128 || m < 1 || m > 128)
+        return fail(nullptr, EMPC_EINVAL, "need 1 <= n <= 128 and 1 <= m <= 128");
+    if (horizon < 1 || knots < 1 || knots > horizon)
+        return fail(nullptr, EMPC_EINVAL, "need horizon >= 1 and 1 <= knots <= horizon");
+    if (pop < 1 || pop > 32768) return fail(nullptr, EMPC_EINVAL, "need 1 <= pop <= 32768");
+    empc_config cfg;
+    if (cfg_in) cfg = *cfg_in; else empc_config_default(&cfg);
+    if (cfg.elite == 0) cfg.elite = std::max(1, pop / 16);
+    if (cfg.elite < 1 || cfg.elite > pop || cfg.elite > 2048)
+        return fail(nullptr, EMPC_EINVAL, "need 1 <= elite <= min(pop, 2048)");
+    if (!(cfg.sigma >= 0.0f) || !std::isfinite(cfg.sigma))
+        return fail(nullptr, EMPC_EINVAL, "sigma must be finite and >= 0");
+    if (cfg.p_cross_256 < 0 || cfg.p_cross_256 > 256 || cfg.p_mutate_256 < 0 ||
+        cfg.p_mutate_256 > 256)
+        return fail(nullptr, EMPC_EINVAL, "probabilities *256 must lie in [0, 256]");
+    if (cfg.gate < 0 || cfg.gate > 2) return fail(nullptr, EMPC_EINVAL, "bad gate mode");
+    if (cfg.precision != EMPC_FP32)
+        return fail(nullptr, EMPC_EUNSUPPORTED, "only FP32 precision is built");
+    if (cfg.refine_steps != 0)
+        return fail(nullptr, EMPC_EUNSUPPORTED, "refinement is not built");
+    if (!finite_all(A, (size_t)n * n) || !finite_all(B, (size_t)n * m) ||
+        !finite_all(Q, (size_t)n * n) || !finite_all(R, (size_t)m * m) ||
+        !finite_all(bounds, (size_t)m * 2))
+        return fail(nullptr, EMPC_EINVAL, "non-finite model, weight or bound");
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (i != j && Q[(size_t)i * n + j] != 0.0)
+                return fail(nullptr, EMPC_EUNSUPPORTED, "Q must be diagonal");
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j)
+            if (i != j && R[(size_t)i * m + j] != 0.0)
+                return fail(nullptr, EMPC_EUNSUPPORTED, "R must be diagonal");
+    for (int i = 0; i < n; ++i)
+        if (Q[(size_t)i * n + i] < 0.0) return fail(nullptr, EMPC_EINVAL, "Q must be >= 0");
+    for (int i = 0; i < m; ++i) {
+        if (R[(size_t)i * m + i] < 0.0) return fail(nullptr, EMPC_EINVAL, "R must be >= 0");
+        if (!(bounds[2 * i] <= bounds[2 * i + 1]))
+            return fail(nullptr, EMPC_EINVAL, "need u_min <= u_max");
+    }
+
+    empc_handle h = new empc_problem_s();
+    h->n = n;
+    h->m = m;
+    h->T = horizon;
+    h->p = knots;
+    h->P = pop;
+    h->E = cfg.elite;
+    h->D = m * knots;
+    h->cfg = cfg;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        free_handle(h);
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+#define EMPC_TRY(call)                                 \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) {                       \
+            empc_status s_ = cuda_fail(nullptr, e_, #call); \
+            free_handle(h);                            \
+            return s_;                                 \
+        }                                              \
+    } while (0)
+    EMPC_TRY(cudaStreamCreate(&h->own_stream));
+    h->stream = h->own_stream;
+
+    // host-side staging of the model in FP32
+    std::vector<float> Dm((size_t)n * n), BT((size_t)m * n), qd(n), rd(m), lo(m), hi(m);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            Dm[(size_t)i * n + j] = (float)(A[(size_t)i * n + j] - (i == j ? 1.0 : 0.0));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < m; ++j) BT[(size_t)j * n + i] = (float)B[(size_t)i * m + j];
+    for (int i = 0; i < n; ++i) qd[i] = (float)Q[(size_t)i * n + i];
+    for (int i = 0; i < m; ++i) {
+        rd[i] = (float)R[(size_t)i * m + i];
+        lo[i] = (float)bounds[2 * i];
+        hi[i] = (float)bounds[2 * i + 1];
+    }
+    std::vector<KnotStep> ks;
+    std::vector<double> w0, w1;
+    std::vector<int> idx;
+    make_knot_table(horizon, knots, ks, w0, w1, idx);
+    // Gram of the knot weights: sum_k u_k' R u_k = sum_i r_i U_i' W U_i with
+    // W tridiagonal: W_aa = sum_k w_ka^2, W_a,a+1 = sum_k w_ka w_k,a+1.
+    std::vector<double> Wd(knots, 0.0), Wo(knots, 0.0);
+    for (int k = 0; k < horizon; ++k) {
+        Wd[idx[k]] += w0[k] * w0[k];
+        if (knots > 1) {
+            Wd[idx[k] + 1] += w1[k] * w1[k];
+            Wo[idx[k]] += w0[k] * w1[k];
+        }
+    }
+    std::vector<float> gram(2 * (size_t)knots);
+    for (int a = 0; a < knots; ++a) {
+        gram[a] = (float)Wd[a];
+        gram[knots + a] = (float)Wo[a];
+    }
+
+    const size_t D = (size_t)h->D;
+    EMPC_TRY(dev_alloc(&h->D_, Dm.size()));
+    EMPC_TRY(dev_alloc(&h->BT, BT.size()));
+    EMPC_TRY(dev_alloc(&h->qdiag, n));
+    EMPC_TRY(dev_alloc(&h->rdiag, m));
+    EMPC_TRY(dev_alloc(&h->gram, gram.size()));
+    EMPC_TRY(dev_alloc(&h->umin, m));
+    EMPC_TRY(dev_alloc(&h->umax, m));
+    EMPC_TRY(dev_alloc(&h->x0, n));
+    EMPC_TRY(dev_alloc(&h->goal, n));
+    EMPC_TRY(dev_alloc(&h->ktab, ks.size()));
+    EMPC_TRY(dev_alloc(&h->pop[0], D * pop));
+    EMPC_TRY(dev_alloc(&h->pop[1], D * pop));
+    EMPC_TRY(dev_alloc(&h->cost, pop));
+    EMPC_TRY(dev_alloc(&h->elite_idx, h->E));
+    EMPC_TRY(dev_alloc(&h->elite_cost, h->E));
+    EMPC_TRY(dev_alloc(&h->best_knots, D));
+    EMPC_TRY(dev_alloc(&h->best_cost, 1));
+    EMPC_TRY(dev_alloc(&h->gen, 1));
+    EMPC_TRY(dev_alloc(&h->status, 1));
+    EMPC_TRY(cudaMallocHost(reinterpret_cast<void**>(&h->stage),
+                            sizeof(float) * (2 * (size_t)n + D + 2)));
+    cudaStream_t st = h->stream;
+    EMPC_TRY(cudaMemcpyAsync(h->D_, Dm.data(), sizeof(float) * Dm.size(), cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->BT, BT.data(), sizeof(float) * BT.size(), cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->qdiag, qd.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->rdiag, rd.data(), sizeof(float) * m, cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->gram, gram.data(), sizeof(float) * gram.size(), cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->umin, lo.data(), sizeof(float) * m, cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->umax, hi.data(), sizeof(float) * m, cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->ktab, ks.data(), sizeof(KnotStep) * ks.size(), cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemsetAsync(h->x0, 0, sizeof(float) * n, st));
+    EMPC_TRY(cudaMemsetAsync(h->goal, 0, sizeof(float) * n, st));
+    EMPC_TRY(cudaMemsetAsync(h->gen, 0, sizeof(uint32_t), st));
+    EMPC_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    EMPC_TRY(cudaStreamSynchronize(st));
+#undef EMPC_TRY
+    empc_status s = autotune(h);
+    if (s != EMPC_OK) {
+        g_thread_error = h->err;
+        free_handle(h);
+        return s;
+    }
+    *out = h;
+    return EMPC_OK;
+}
+
+empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal, int generations,
+                       float* best_knots, float* best_cost) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!x0 || !x_goal || !best_knots || !best_cost)
+        return fail(h, EMPC_EINVAL, "NULL x0, x_goal or output pointer");
+    if (generations < 1) return fail(h, EMPC_EINVAL, "generations must be >= 1");
+    if (!finite_all(x0, h->n) || !finite_all(x_goal, h->n))
+        return fail(h, EMPC_EINVAL, "non-finite x0 or x_goal");
+    float* st_in = h->stage;
+    for (int i = 0; i < h->n; ++i) {
+        st_in[i] = (float)x0[i];
+        st_in[h->n + i] = (float)x_goal[i];
+    }
+    EMPC_CUDA(h, cudaMemcpyAsync(h->x0, st_in, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(h->goal, st_in + h->n, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
+    EMPC_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    empc_status s = run_generations(h, generations);
+    if (s != EMPC_OK) return s;
+    float* st_out = h->stage + 2 * h->n;
+    EMPC_CUDA(h, cudaMemcpyAsync(st_out, h->best_knots, sizeof(float) * h->D, cudaMemcpyDeviceToHost, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(st_out + h->D, h->best_cost, sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(st_out + h->D + 1, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+    std::memcpy(best_knots, st_out, sizeof(float) * h->D);
+    *best_cost = st_out[h->D];
+    int status_bits;
+    std::memcpy(&status_bits, st_out + h->D + 1, sizeof(int));
+    if (status_bits & 1) return fail(h, EMPC_ENONFINITE, "best cost is not finite");
+    return EMPC_OK;
+}
+
+empc_status empc_solve_device(empc_handle h, const float* dev_x0, const float* dev_goal,
+                              int generations, float* dev_best_knots, float* dev_best_cost) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!dev_x0 || !dev_goal || !dev_best_knots || !dev_best_cost)
+        return fail(h, EMPC_EINVAL, "NULL device pointer");
+    if (generations < 1) return fail(h, EMPC_EINVAL, "generations must be >= 1");
+    EMPC_CUDA(h, cudaMemcpyAsync(h->x0, dev_x0, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(h->goal, dev_goal, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+    empc_status s = run_generations(h, generations);
+    if (s != EMPC_OK) return s;
+    EMPC_CUDA(h, cudaMemcpyAsync(dev_best_knots, h->best_knots, sizeof(float) * h->D, cudaMemcpyDeviceToDevice, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(dev_best_cost, h->best_cost, sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    return EMPC_OK;
+}
+
+empc_status empc_evaluate(empc_handle h, const float* dev_x0, const float* dev_goal,
+                          const float* dev_pop, int count, float* dev_cost) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!dev_x0 || !dev_goal || !dev_pop || !dev_cost)
+        return fail(h, EMPC_EINVAL, "NULL device pointer");
+    if (count < 0) return fail(h, EMPC_EINVAL, "count must be >= 0");
+    if (count == 0) return EMPC_OK;
+    RolloutArgs a = base_args(h);
+    a.x0 = dev_x0;
+    a.goal = dev_goal;
+    a.mode = empc::kEval;
+    a.P = count;
+    a.pop_in = dev_pop;
+    a.cost = dev_cost;
+    a.gen = nullptr;
+    EMPC_CUDA(h, empc::launch_rollout(a, h->shape, h->stream));
+    return EMPC_OK;
+}
+
+empc_status empc_get_state(empc_handle h, float* dev_pop, float* dev_cost, int* dev_elite) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!h->has_pop) return fail(h, EMPC_ESTATE, "no population yet (solve first)");
+    if (dev_pop)
+        EMPC_CUDA(h, cudaMemcpyAsync(dev_pop, h->pop[h->cur], sizeof(float) * h->D * h->P,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+    if (dev_cost)
+        EMPC_CUDA(h, cudaMemcpyAsync(dev_cost, h->cost, sizeof(float) * h->P,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+    if (dev_elite)
+        EMPC_CUDA(h, cudaMemcpyAsync(dev_elite, h->elite_idx, sizeof(int) * h->E,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+    return EMPC_OK;
+}
+
+empc_status empc_set_state(empc_handle h, const float* dev_pop, const float* dev_cost,
+                           const int* dev_elite) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!dev_pop || !dev_cost || !dev_elite)
+        return fail(h, EMPC_EINVAL, "population, costs and elites are all required");
+    EMPC_CUDA(h, cudaMemcpyAsync(h->pop[h->cur], dev_pop, sizeof(float) * h->D * h->P,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(h->cost, dev_cost, sizeof(float) * h->P,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    EMPC_CUDA(h, cudaMemcpyAsync(h->elite_idx, dev_elite, sizeof(int) * h->E,
+                                 cudaMemcpyDeviceToDevice, h->stream));
+    h->has_pop = true;
+    return EMPC_OK;
+}
+
+empc_status empc_reset(empc_handle h) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    h->has_pop = false;
+    return EMPC_OK;
+}
+
+empc_status empc_set_stream(empc_handle h, void* stream) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+    return EMPC_OK;
+}
+
+empc_status empc_get_info(empc_handle h, empc_info* info) {
+    if (!h || !info) return fail(h, EMPC_EINVAL, "NULL handle or info");
+    std::memset(info, 0, sizeof(*info));
+    info->n = h->n;
+    info->m = h->m;
+    info->horizon = h->T;
+    info->knots = h->p;
+    info->pop = h->P;
+    info->elite = h->E;
+    info->generation = h->gen_host;
+    info->tile_nx = h->shape.nx;
+    info->tile_rows = h->shape.rows;
+    info->tile_cands = h->shape.cands;
+    info->tile_groups = h->shape.groups;
+    info->tile_kind = h->shape.kind;
+    info->threads_per_cta = empc::rollout_threads(h->shape, h->n);
+    info->smem_bytes = (int)empc::rollout_smem_bytes(h->shape, h->n, h->m, h->p, h->T);
+    const int ptile = empc::rollout_cands_per_cta(h->shape, h->n);
+    info->ctas = (h->P + ptile - 1) / ptile;
+    info->tuned_us = h->tuned_us;
+    info->refine_lr = h->cfg.refine_lr;
+    return EMPC_OK;
+}
+
+empc_status empc_time_generation(empc_handle h, int reps, float* rollout_us, float* select_us) {
+    if (!h || !rollout_us || !select_us || reps < 1)
+        return fail(h, EMPC_EINVAL, "need a handle, reps >= 1 and two outputs");
+    if (!h->has_pop) return fail(h, EMPC_ESTATE, "no population yet (solve first)");
+    cudaEvent_t ev[3];
+    for (auto& e : ev) EMPC_CUDA(h, cudaEventCreate(&e));
+    double t_roll = 0.0, t_sel = 0.0;
+    empc_status s = EMPC_OK;
+    for (int r = 0; r < reps && s == EMPC_OK; ++r) {
+        RolloutArgs a = base_args(h);
+        a.mode = empc::kWarm;
+        a.pop_in = h->pop[h->cur];
+        a.pop_out = h->pop[h->cur ^ 1];
+        a.cost = h->cost;
+        a.elite_idx = h->elite_idx;
+        cudaError_t e = cudaEventRecord(ev[0], h->stream);
+        if (e == cudaSuccess) e = empc::launch_rollout(a, h->shape, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+        if (e == cudaSuccess)
+            e = empc::launch_select(h->cost, h->P, h->E, h->pop[h->cur ^ 1], h->D, h->elite_idx,
+                                    h->elite_cost, h->best_knots, h->best_cost, h->gen,
+                                    h->status, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        if (e != cudaSuccess) {
+            s = cuda_fail(h, e, "empc_time_generation");
+            break;
+        }
+        float a_ms = 0, b_ms = 0;
+        cudaEventElapsedTime(&a_ms, ev[0], ev[1]);
+        cudaEventElapsedTime(&b_ms, ev[1], ev[2]);
+        t_roll += a_ms;
+        t_sel += b_ms;
+        h->cur ^= 1;
+        h->gen_host += 1;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (s != EMPC_OK) return s;
+    *rollout_us = (float)(1000.0 * t_roll / reps);
+    *select_us = (float)(1000.0 * t_sel / reps);
+    return EMPC_OK;
+}
+
+void empc_destroy(empc_handle h) { free_handle(h); }
+
+const char* empc_last_error(empc_handle h) {
+    return h ? h->err.c_str() : g_thread_error.c_str();
+}
+
+empc_status empc_discretize_zoh(const double* Ac, const double* Bc, int n, int m, double dt,
+                                double* Ad, double* Bd) {
+    if (!Ac || !Bc || !Ad || !Bd) return fail(nullptr, EMPC_EINVAL, "NULL pointer");
+    if (n < 1 || m < 0 || !std::isfinite(dt) || dt < 0.0)
+        return fail(nullptr, EMPC_EINVAL, "need n >= 1, m >= 0, finite dt >= 0");
+    if (!finite_all(Ac, (size_t)n * n) || !finite_all(Bc, (size_t)n * m))
+        return fail(nullptr, EMPC_EINVAL, "non-finite Ac or Bc");
+    const int N = n + m;
+    std::vector<double> M((size_t)N * N, 0.0), E;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) M[(size_t)i * N + j] = Ac[(size_t)i * n + j] * dt;
+        for (int j = 0; j < m; ++j) M[(size_t)i * N + n + j] = Bc[(size_t)i * m + j] * dt;
+    }
+    if (!expm_pade6(M, N, E)) return fail(nullptr, EMPC_EINVAL, "singular Pade denominator");
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) Ad[(size_t)i * n + j] = E[(size_t)i * N + j];
+        for (int j = 0; j < m; ++j) Bd[(size_t)i * m + j] = E[(size_t)i * N + n + j];
+    }
+    return EMPC_OK;
+}
+
+}  // extern "C"

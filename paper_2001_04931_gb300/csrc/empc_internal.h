@@ -1,0 +1,87 @@
+// Internal declarations shared by the EMPC CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace empc {
+
+// Breeding mode of the fused breed + rollout + cost kernel.
+enum BreedMode : int { kEval = 0, kCold = 1, kWarm = 2 };
+
+// Per-step knot table entry: u_k = w0 U_idx1 + w1 U_idx1+1 (Sec. IV-C).
+struct KnotStep {
+    int idx1;
+    float w0;
+    float w1;
+    int pad;
+};
+
+// Everything the fused kernel reads.  Device pointers, FP32.
+struct RolloutArgs {
+    // model
+    const float* D;      // [n][n] row-major, D = A_d - I (delta form)
+    const float* BT;     // [m][n] = B_d transposed
+    const float* qdiag;  // [n]   diagonal of Q
+    const float* rdiag;  // [m]   diagonal of R
+    const float* gram;   // [2p]  input-cost Gram: diag W_aa (p), off-diag W_a,a+1 (p)
+    const KnotStep* ktab;  // [T]
+    const float* x0;     // [n]
+    const float* goal;   // [n]
+    const float* umin;   // [m]
+    const float* umax;   // [m]
+    int n, m, T, p, P;
+    // population
+    const float* pop_in;  // warm: previous population; eval: population to score
+    float* pop_out;       // cold/warm: the bred population (SoA [m p][P])
+    float* cost;          // [P]
+    const int* elite_idx;  // [E] previous elites in rank order (warm)
+    int E;
+    // breeding
+    int mode;
+    uint64_t seed;
+    const uint32_t* gen;  // device generation counter
+    float sigma;
+    int pc256, pm256, gate;
+    // optional checkpoint output for the adjoint (may be null)
+    float* ckpt;   // [T/ckpt_every + 1][n][P]
+    int ckpt_every;
+};
+
+// Rollout tile.  kind 0 (block): ceil(n/rows) threads per candidate group,
+// `groups` candidate groups per CTA, one block barrier per step.  kind 1
+// (warp): each warp owns whole candidates (32/nrg groups of `cands`), `groups`
+// warps per CTA, one warp barrier per step.
+struct TileShape {
+    int kind;   // 0 block, 1 warp
+    int nx;     // compiled state dimension (>= n)
+    int rows;   // state rows per thread
+    int cands;  // candidates per thread (1, 2 or 4)
+    int groups; // candidate groups per CTA (block) or warps per CTA (warp)
+};
+
+// Launch the fused kernel.  Returns cudaErrorInvalidConfiguration when the
+// shape is not compiled or does not fit.
+cudaError_t launch_rollout(const RolloutArgs& a, const TileShape& s, cudaStream_t st);
+// Shapes compiled for state dimension n, in autotuning order.
+int rollout_shapes(int n, TileShape* out, int cap);
+// Whether the shape fits (registers, threads, shared memory) for this problem.
+bool rollout_shape_supported(const TileShape& s, int n, int m, int p, int T);
+size_t rollout_smem_bytes(const TileShape& s, int n, int m, int p, int T);
+int rollout_threads(const TileShape& s, int n);
+int rollout_cands_per_cta(const TileShape& s, int n);
+
+// Per-family entry points (rollout_block.cu, rollout_warp.cu).
+cudaError_t launch_rollout_block(const RolloutArgs& a, const TileShape& s, cudaStream_t st);
+cudaError_t launch_rollout_warp(const RolloutArgs& a, const TileShape& s, cudaStream_t st);
+int block_max_threads(const TileShape& s);
+int warp_max_threads(const TileShape& s);
+int warp_nrg(int nx);
+
+// Elite selection: E lowest of P costs by (cost, index), NaN as +inf.
+// Writes elite_idx[E], elite_cost[E], best_knots[m p] and increments *gen.
+cudaError_t launch_select(const float* cost, int P, int E, const float* pop, int D,
+                          int* elite_idx, float* elite_cost, float* best_knots,
+                          float* best_cost, uint32_t* gen, int* status, cudaStream_t st);
+
+}  // namespace empc

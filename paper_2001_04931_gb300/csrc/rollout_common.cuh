@@ -1,0 +1,321 @@
+// Device helpers shared by the two fused breed + rollout + cost kernels.
+//
+// Both kernels evaluate, per candidate, Algorithm 1's simulation and stage
+// cost over the horizon (Sec. V), in the parameterized form of Sec. IV-C:
+//
+//   x_{k+1} = x_k + D x_k + w0_k BU_idx1(k) + w1_k BU_idx1(k)+1,  D = A_d - I,
+//
+// with BU_j = B_d U_j the force of knot j, formed once per knot segment.
+// The delta form keeps FP32 rounding relative to the increment.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "draws.cuh"
+#include "empc_internal.h"
+
+namespace empc {
+
+template <int C>
+__device__ __forceinline__ void load_vec(const float* p, float (&v)[C]) {
+    if constexpr (C == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (C == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
+template <int C>
+__device__ __forceinline__ void store_vec(float* p, const float (&v)[C]) {
+    if constexpr (C == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (C == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+        *p = v[0];
+    }
+}
+
+__host__ __device__ __forceinline__ int round_up(int v, int to) { return (v + to - 1) / to * to; }
+
+// out[r][c] = sum_i B_d[row0 + r][i] U[i*p + a][col0 + c]  (knot force B_d U_a).
+// BTs holds B_d transposed with leading dimension ldb (rows beyond n zero).
+template <int R, int C>
+__device__ __forceinline__ void knot_force(const float* BTs, int ldb, const float* Us, int xs,
+                                           int m, int p, int a, int row0, int col0,
+                                           float (&out)[R][C]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[r][c] = 0.0f;
+    for (int i = 0; i < m; ++i) {
+        float u[C];
+        load_vec<C>(Us + (i * p + a) * xs + col0, u);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float b = BTs[i * ldb + row0 + r];
+#pragma unroll
+            for (int c = 0; c < C; ++c) out[r][c] = fmaf(b, u[c], out[r][c]);
+        }
+    }
+}
+
+// acc[r][c] += sum_k d[r][k] X[k][c]: two interleaved partial sums (even and
+// odd k) double the independent FMA chains; the split is part of the fixed
+// summation order, identical for every candidate.
+template <int NX, int R, int C>
+__device__ __forceinline__ void state_product(const float (&d)[R][NX], const float* Xb, int xs,
+                                              float (&acc)[R][C]) {
+    float odd[R][C];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) odd[r][c] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+        float xv[C];
+        load_vec<C>(Xb + k * xs, xv);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (k & 1) odd[r][c] = fmaf(d[r][k], xv[c], odd[r][c]);
+                else acc[r][c] = fmaf(d[r][k], xv[c], acc[r][c]);
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] += odd[r][c];
+}
+
+// Breed (cold / warm, Algorithm 1) or load (eval) the knots of candidates
+// c0 .. c0+count-1 into Us[q][t] (leading dimension xs); bred knots also go
+// to pop_out.  Work is spread over `nthr` threads with index `tid`; WARP
+// selects warp- or block-level synchronization.
+template <bool WARP>
+__device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, int c0,
+                           int count, uint32_t gen, int tid, int nthr) {
+    const int D = a.m * a.p;
+    const int nquad = (D + 3) >> 2;
+    if (a.mode == kWarm) {
+        for (int t = tid; t < count; t += nthr) {
+            const int c = c0 + t;
+            int s1 = 0, s2 = -1;
+            if (c < a.P) {
+                if (c < a.E) {
+                    s1 = a.elite_idx[c];
+                } else {
+                    const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawParents, 0u);
+                    s1 = a.elite_idx[parent_rank(o.w[0], a.E)];
+                    s2 = a.elite_idx[parent_rank(o.w[1], a.E)];
+                }
+            }
+            par[2 * t] = s1;
+            par[2 * t + 1] = s2;
+        }
+        if (WARP) __syncwarp(); else __syncthreads();
+    }
+    for (int it = tid; it < nquad * count; it += nthr) {
+        const int t = it % count;
+        const int quad = it / count;
+        const int c = c0 + t;
+        const int q0 = quad * 4;
+        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (c < a.P) {
+            if (a.mode == kEval) {
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (q0 + w < D) v[w] = a.pop_in[(size_t)(q0 + w) * a.P + c];
+            } else if (a.mode == kCold) {
+                const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawInit, (uint32_t)quad);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int q = q0 + w;
+                    if (q < D) {
+                        const int i = q / a.p;
+                        const float lo = a.umin[i], hi = a.umax[i];
+                        v[w] = clamp_to(__fmaf_rn(__fsub_rn(hi, lo), unit_closed_open(o.w[w]), lo),
+                                        lo, hi);
+                    }
+                }
+            } else {
+                const int s1 = par[2 * t], s2 = par[2 * t + 1];
+                if (s2 < 0) {
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+                        if (q0 + w < D) v[w] = a.pop_in[(size_t)(q0 + w) * a.P + s1];
+                } else {
+                    const uint32_t cross =
+                        draw(a.seed, (uint32_t)c, gen, kDrawCross, (uint32_t)(quad >> 2)).w[quad & 3];
+                    Words4 gw;
+                    uint32_t gate_blk = 0xFFFFFFFFu;
+                    float z[4];
+                    bool have_z = false;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int q = q0 + w;
+                        if (q >= D) continue;
+                        const int i = q / a.p;
+                        const uint32_t cb = (cross >> (8 * w)) & 0xFFu;
+                        const float mate = (cb < (uint32_t)a.pc256)
+                                               ? a.pop_in[(size_t)q * a.P + s2]
+                                               : a.pop_in[(size_t)q * a.P + s1];
+                        bool mut = true;
+                        if (a.gate != 2) {
+                            const uint32_t gb = (a.gate == 0) ? (uint32_t)i : (uint32_t)q;
+                            if ((gb >> 4) != gate_blk) {
+                                gate_blk = gb >> 4;
+                                gw = draw(a.seed, (uint32_t)c, gen, kDrawGate, gate_blk);
+                            }
+                            mut = ((gw.w[(gb >> 2) & 3u] >> (8u * (gb & 3u))) & 0xFFu) <
+                                  (uint32_t)a.pm256;
+                        }
+                        float val = mate;
+                        if (mut) {
+                            if (!have_z) {
+                                const Words4 nz =
+                                    draw(a.seed, (uint32_t)c, gen, kDrawNoise, (uint32_t)quad);
+                                gauss_pair(nz.w[0], nz.w[1], &z[0], &z[1]);
+                                gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
+                                have_z = true;
+                            }
+                            val = __fmaf_rn(a.sigma, z[w], mate);
+                        }
+                        v[w] = clamp_to(val, a.umin[i], a.umax[i]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int q = q0 + w;
+            if (q < D) {
+                Us[q * xs + t] = v[w];
+                if (a.mode != kEval && c < a.P) a.pop_out[(size_t)q * a.P + c] = v[w];
+            }
+        }
+    }
+    if (WARP) __syncwarp(); else __syncthreads();
+}
+
+// Input cost sum_k u_k' R u_k of one candidate restricted to inputs
+// i0, i0 + istep, ..., in closed form through the tridiagonal Gram matrix of
+// the knot weights (W_aa = gram[a], W_a,a+1 = gram[p + a]).
+__device__ __forceinline__ float input_cost_part(const RolloutArgs& a, const float* Us, int xs,
+                                                 int col, int i0, int istep) {
+    const int p = a.p;
+    float Ju = 0.0f;
+    for (int i = i0; i < a.m; i += istep) {
+        float s = 0.0f;
+        for (int j = 0; j < p; ++j) {
+            const float u = Us[(i * p + j) * xs + col];
+            s = fmaf(a.gram[j] * u, u, s);
+            if (j + 1 < p) s = fmaf(2.0f * a.gram[p + j] * u, Us[(i * p + j + 1) * xs + col], s);
+        }
+        Ju = fmaf(a.rdiag[i], s, Ju);
+    }
+    return Ju;
+}
+
+__device__ __forceinline__ float finite_or_inf(float v) {
+    return (v == v) ? v : __int_as_float(0x7f800000);
+}
+
+}  // namespace empc
+
+namespace empc {
+
+// The horizon loop for one thread: rows row0 .. row0+R-1 of C candidates
+// (columns col0 .. col0+C-1 of the state tile X[2][xrows][xs]).  D rows are
+// in registers; BU pairs are refreshed at knot-segment changes; the stage
+// cost is accumulated in 16-step blocks.  One barrier (warp or block) per
+// step separates the double-buffered state reads from the writes.
+template <int NX, int R, int C, bool WARP>
+__device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (&d)[R][NX],
+                                             float* X, int xrows, int xs, const float* BTs,
+                                             int ldb, const float* Us, const KnotStep* ks,
+                                             int row0, int col0, float (&xo)[R][C],
+                                             const float (&qd)[R], const float (&gl)[R],
+                                             float (&jsum)[C]) {
+    float bua[R][C], bub[R][C];
+    int seg = -1;
+    float jtot[C], jblk[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) jtot[c] = jblk[c] = 0.0f;
+    int buf = 0;
+    for (int k = 0; k < a.T; ++k) {
+        const KnotStep st = ks[k];
+        if (st.idx1 != seg) {
+            if (st.idx1 == seg + 1 && seg >= 0) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) bua[r][c] = bub[r][c];
+            } else {
+                knot_force<R, C>(BTs, ldb, Us, xs, a.m, a.p, st.idx1, row0, col0, bua);
+            }
+            if (st.idx1 + 1 < a.p) {
+                knot_force<R, C>(BTs, ldb, Us, xs, a.m, a.p, st.idx1 + 1, row0, col0, bub);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) bub[r][c] = 0.0f;
+            }
+            seg = st.idx1;
+        }
+        float acc[R][C];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[r][c] = fmaf(st.w1, bub[r][c], st.w0 * bua[r][c]);
+        state_product<NX, R, C>(d, X + buf * xrows * xs + col0, xs, acc);
+        float* Xn = X + (buf ^ 1) * xrows * xs + col0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float xn[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                xn[c] = xo[r][c] + acc[r][c];
+                xo[r][c] = xn[c];
+                const float e = xn[c] - gl[r];
+                jblk[c] = fmaf(qd[r] * e, e, jblk[c]);
+            }
+            store_vec<C>(Xn + (row0 + r) * xs, xn);
+        }
+        if ((k & 15) == 15) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                jtot[c] += jblk[c];
+                jblk[c] = 0.0f;
+            }
+        }
+        if (WARP) __syncwarp(); else __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) jsum[c] = jtot[c] + jblk[c];
+}
+
+// Load this thread's D rows, Q diagonal, goal and initial state.
+template <int NX, int R, int C>
+__device__ __forceinline__ void load_rows(const RolloutArgs& a, int row0, float (&d)[R][NX],
+                                          float (&qd)[R], float (&gl)[R], float (&xo)[R][C]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = row0 + r;
+        const bool ok = row < a.n;
+#pragma unroll
+        for (int k = 0; k < NX; ++k) d[r][k] = (ok && k < a.n) ? a.D[row * a.n + k] : 0.0f;
+        qd[r] = ok ? a.qdiag[row] : 0.0f;
+        gl[r] = ok ? a.goal[row] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) xo[r][c] = ok ? a.x0[row] : 0.0f;
+    }
+}
+
+}  // namespace empc

@@ -134,6 +134,32 @@ empc_status empc_evaluate(empc_handle h, const float* dev_x0, const float* dev_g
                           const float* dev_pop, int count, float* dev_cost);
 
 /*
+ * empc_evaluate_noalloc - empc_evaluate for callers that cannot allocate GPU
+ * memory (a real-time control loop where cudaMalloc/cudaFree could stall
+ * the device for an unbounded time, or a process whose GPU memory another
+ * allocator reserved up front).  The paper has no counterpart; it is a
+ * library addition.
+ *   A [n*n], B [n*m], Q [n*n] (diagonal), R [m*m] (diagonal): host FP64,
+ *     the same model as empc_create; horizon T and knots p as there.
+ *   dev_x0 [n], dev_goal [n], dev_pop [m*p][count] (SoA, stride count):
+ *     device FP32 inputs; dev_cost [count]: device FP32 output.
+ *   stream: a cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Allocates nothing: the per-problem tables live in one fixed device array
+ * of 12,544 floats (49 KiB) that every device loading the library holds
+ * until the process exits.  Limits: n <= 64, m <= 64, T <= 1024, p <= 64;
+ * larger sizes return EMPC_EINVAL (use the handle API).  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  Every call shares the array (each call rewrites what
+ * it uses), so calls whose GPU work overlaps race and give wrong costs:
+ * order them on one stream.  Non-diagonal Q or R: EMPC_EUNSUPPORTED.
+ */
+empc_status empc_evaluate_noalloc(const double* A, const double* B, const double* Q,
+                                  const double* R, int n, int m, int horizon, int knots,
+                                  const float* dev_x0, const float* dev_goal,
+                                  const float* dev_pop, int count, float* dev_cost,
+                                  void* stream);
+
+/*
  * empc_get_state - copy the current population [m*p][P], its costs [P] and
  * the elite indices [E] in rank order (best first) to device buffers; any
  * pointer may be NULL.  Asynchronous.  EMPC_ESTATE before the first solve.

@@ -70,6 +70,8 @@ _SIGNATURES = {
     "empc_discretize_zoh": (_i, [_dp, _dp, _i, _i, ctypes.c_double, _dp, _dp]),
     "empc_time_generation": (_i, [_h, _i, _fp, _fp]),
     "empc_measure_fp32_peak": (_i, [_dp]),
+    "empc_evaluate_noalloc": (_i, [_dp, _dp, _dp, _dp, _i, _i, _i, _i, _vp, _vp, _vp, _i,
+                                  _vp, _vp]),
 }
 
 
@@ -136,6 +138,17 @@ def discretize_zoh(Ac, Bc, dt):
     Ad, Bd = np.zeros((n, n)), np.zeros((n, m))
     check(_lib.empc_discretize_zoh(_ptr(Ac), _ptr(Bc), n, m, float(dt), _ptr(Ad), _ptr(Bd)))
     return Ad, Bd
+
+
+def evaluate_noalloc(A, B, Q, R, horizon, knots, x0, x_goal, pop, cost, stream=None):
+    """Population costs without device allocation (tables in a fixed device
+    array; see empc_evaluate_noalloc in include/empc.h).  x0, x_goal, pop
+    [m*p, count] and cost [count] are CUDA tensors; asynchronous on `stream`."""
+    A, B, Q, R = _d(A), _d(B), _d(Q), _d(R)
+    n, m = B.shape
+    check(_lib.empc_evaluate_noalloc(_ptr(A), _ptr(B), _ptr(Q), _ptr(R), n, m, int(horizon),
+                                     int(knots), _dev(x0), _dev(x_goal), _dev(pop),
+                                     int(pop.shape[1]), _dev(cost), stream))
 
 
 def measure_fp32_peak():

@@ -359,6 +359,11 @@ bool expm_pade6(const std::vector<double>& A, int N, std::vector<double>& out) {
 
 }  // namespace
 
+int empc::set_thread_error(int s, const char* msg) {
+    g_thread_error = msg;
+    return s;
+}
+
 extern "C" {
 
 void empc_config_default(empc_config* cfg) {

@@ -84,4 +84,7 @@ cudaError_t launch_select(const float* cost, int P, int E, const float* pop, int
                           int* elite_idx, float* elite_cost, float* best_knots,
                           float* best_cost, uint32_t* gen, int* status, cudaStream_t st);
 
+// Record a failure message for empc_last_error(NULL) on this thread; returns s.
+int set_thread_error(int s, const char* msg);
+
 }  // namespace empc

@@ -80,6 +80,7 @@ typedef struct {
     float tuned_us;          /* autotuner's best rollout time (microseconds), 0 if forced */
     float refine_lr;         /* projected-gradient step in use */
     int tile_kind;           /* 0: block-synchronous rollout, 1: warp-synchronous */
+    int ckpt_every;          /* adjoint checkpoint interval in use */
 } empc_info;
 
 /* Defaults listed in empc_config. */
@@ -158,6 +159,21 @@ empc_status empc_evaluate_noalloc(const double* A, const double* B, const double
                                   const float* dev_x0, const float* dev_goal,
                                   const float* dev_pop, int count, float* dev_cost,
                                   void* stream);
+
+/*
+ * empc_grad - adjoint gradient of the cost (the empc_create formula) with
+ * respect to the knots, for dev_pop [m*p][count] (SoA, stride count):
+ * dev_grad [m*p][count] (same layout) and dev_cost [count]; either output
+ * may be NULL, not both.  The forward pass keeps the state every ckpt_every
+ * steps and the backward pass recomputes each segment from its checkpoint,
+ * so memory is O(T/ckpt_every + ckpt_every) states per candidate.  FP32.
+ * Needs n <= 64 (else EMPC_EUNSUPPORTED).  Asynchronous.  The paper's
+ * optimizer is gradient-free; this is a library addition (with
+ * cfg.refine_steps > 0 the elites of every generation take that many
+ * projected-gradient steps U <- clip(U - eta dJ/dU) before the next one).
+ */
+empc_status empc_grad(empc_handle h, const float* dev_x0, const float* dev_goal,
+                      const float* dev_pop, int count, float* dev_grad, float* dev_cost);
 
 /*
  * empc_get_state - copy the current population [m*p][P], its costs [P] and

@@ -286,8 +286,10 @@ class EMPC:
     Mirrors the library's call semantics: the population persists between
     solve() calls (warm start); generation numbers count up across calls and
     key the random draws; reset() makes the next generation a cold start.
-    With refine_steps > 0 the elites are refined by projected gradient before
-    each warm-start breeding.
+    With refine_steps > 0 the elites are refined between generations: the
+    children are bred from the elites as selected, and slot e of the new
+    population holds elite e after `refine_steps` projected-gradient steps
+    (instead of the unchanged copy).
     """
 
     def __init__(self, model, P, E, seed, sigma, pc256=128, pm256=128, gate_mode=0,
@@ -309,12 +311,16 @@ class EMPC:
     def reset(self):
         self.pop = None
 
-    def refine_elites(self, x0, g):
+    def refined_elites(self, x0, g, pop=None, elite=None):
+        """[m*p, E] float64: each elite after refine_steps projected steps."""
+        pop = self.pop if pop is None else pop
+        elite = self.elite if elite is None else elite
         M = self.model
-        for e in self.elite:
-            U = self.pop[:, e].astype(np.float64)
-            self.pop[:, e] = M.refine(x0, g, U, self.refine_steps,
-                                      self.refine_eta).astype(np.float32)
+        out = np.zeros((pop.shape[0], len(elite)))
+        for r, e in enumerate(elite):
+            out[:, r] = M.refine(x0, g, pop[:, e].astype(np.float64), self.refine_steps,
+                                 self.refine_eta)
+        return out
 
     def generation(self, x0, g):
         M = self.model
@@ -322,11 +328,11 @@ class EMPC:
             pop = breed_cold(self.seed, self.gen, self.umin32, self.umax32, M.m, M.p,
                              self.P)
         else:
-            if self.refine_steps > 0:
-                self.refine_elites(x0, g)
             pop = breed_warm(self.seed, self.gen, self.pop, self.elite, self.umin32,
                              self.umax32, M.m, M.p, self.sigma, self.pc256, self.pm256,
                              self.gate_mode)
+            if self.refine_steps > 0:
+                pop[:, :self.E] = self.refined_elites(x0, g).astype(np.float32)
         self.gen += 1
         self.pop = pop
         self.cost = M.cost_population(x0, g, pop)

@@ -43,7 +43,7 @@ class empc_info(ctypes.Structure):
                 ("tile_groups", ctypes.c_int), ("threads_per_cta", ctypes.c_int),
                 ("smem_bytes", ctypes.c_int), ("ctas", ctypes.c_int),
                 ("tuned_us", ctypes.c_float), ("refine_lr", ctypes.c_float),
-                ("tile_kind", ctypes.c_int)]
+                ("tile_kind", ctypes.c_int), ("ckpt_every", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -60,6 +60,7 @@ _SIGNATURES = {
     "empc_solve": (_i, [_h, _dp, _dp, _i, _fp, _fp]),
     "empc_solve_device": (_i, [_h, _vp, _vp, _i, _vp, _vp]),
     "empc_evaluate": (_i, [_h, _vp, _vp, _vp, _i, _vp]),
+    "empc_grad": (_i, [_h, _vp, _vp, _vp, _i, _vp, _vp]),
     "empc_get_state": (_i, [_h, _vp, _vp, _vp]),
     "empc_set_state": (_i, [_h, _vp, _vp, _vp]),
     "empc_reset": (_i, [_h]),
@@ -207,6 +208,11 @@ class Problem:
         """Costs of pop [m*p, count] (CUDA tensors) into cost [count]."""
         check(_lib.empc_evaluate(self.handle, _dev(x0), _dev(x_goal), _dev(pop),
                                  int(pop.shape[1]), _dev(cost)), self.handle)
+
+    def grad(self, x0, x_goal, pop, grad=None, cost=None):
+        """Adjoint dJ/dU of pop [m*p, count] into grad (same shape) and cost."""
+        check(_lib.empc_grad(self.handle, _dev(x0), _dev(x_goal), _dev(pop), int(pop.shape[1]),
+                             _dev(grad), _dev(cost)), self.handle)
 
     def get_state(self, pop=None, cost=None, elite=None):
         check(_lib.empc_get_state(self.handle, _dev(pop), _dev(cost), _dev(elite)),

@@ -62,6 +62,12 @@ struct empc_problem_s {
     uint64_t gen_host = 0;
     TileShape shape{};
     float tuned_us = 0.0f;
+    // refinement (projected gradient on the elites) and the adjoint
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int ce = 1;            // checkpoint interval
+    float eta = 0.0f;      // refinement step
+    int grad_cands = 1, grad_wpc = 2;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::string err;
 };
@@ -150,8 +156,32 @@ RolloutArgs base_args(empc_handle h) {
     return a;
 }
 
-// One generation: breed (cold or warm) + rollout + cost into pop[parity^1],
-// then elite selection.
+empc::GradArgs grad_args(empc_handle h) {
+    empc::GradArgs g{};
+    g.D = h->D_;
+    g.BT = h->BT;
+    g.qdiag = h->qdiag;
+    g.rdiag = h->rdiag;
+    g.gram = h->gram;
+    g.ktab = h->ktab;
+    g.x0 = h->x0;
+    g.goal = h->goal;
+    g.umin = h->umin;
+    g.umax = h->umax;
+    g.n = h->n;
+    g.m = h->m;
+    g.T = h->T;
+    g.p = h->p;
+    g.ce = h->ce;
+    g.eta = h->eta;
+    return g;
+}
+
+// One generation into pop[parity^1], then elite selection.  Cold: breed +
+// rollout + cost of every candidate.  Warm: the children (slots E..P-1) are
+// bred from the previous elites and rolled out; with refinement enabled the
+// elites themselves are refined by projected gradient on a second stream at
+// the same time and written, with their costs, to slots 0..E-1.
 cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_t st) {
     RolloutArgs a = base_args(h);
     a.mode = cold ? empc::kCold : empc::kWarm;
@@ -159,11 +189,107 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
     a.pop_out = h->pop[parity ^ 1];
     a.cost = h->cost;
     a.elite_idx = h->elite_idx;
-    cudaError_t e = empc::launch_rollout(a, h->shape, st);
+    const bool refine = !cold && h->cfg.refine_steps > 0;
+    cudaError_t e = cudaSuccess;
+    if (refine) {
+        a.cand_begin = h->E;
+        empc::GradArgs g = grad_args(h);
+        g.pop_in = h->pop[parity];
+        g.ld_in = h->P;
+        g.index = h->elite_idx;
+        g.count = h->E;
+        g.cost = h->cost;
+        g.pop_out = h->pop[parity ^ 1];
+        g.ld_out = h->P;
+        g.steps = h->cfg.refine_steps;
+        if ((e = cudaEventRecord(h->ev_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0)) != cudaSuccess) return e;
+        e = empc::launch_grad(g, h->shape.nx, h->grad_cands, h->grad_wpc, h->aux_stream);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(h->ev_join, h->aux_stream)) != cudaSuccess) return e;
+    }
+    // Programmatic dependent launch between the generation's kernels (not
+    // across the refinement fork/join).
+    a.pdl = refine ? 0 : 1;
+    e = empc::launch_rollout(a, h->shape, st);
     if (e != cudaSuccess) return e;
+    if (refine && (e = cudaStreamWaitEvent(st, h->ev_join, 0)) != cudaSuccess) return e;
     return empc::launch_select(h->cost, h->P, h->E, h->pop[parity ^ 1], h->D, h->elite_idx,
                                h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
-                               st);
+                               st, !refine);
+}
+
+// Largest eigenvalue of the condensed Hessian H (J = U'HU + 2f'U + c) in
+// FP64, for the projected-gradient step 1/L with L = 2 lambda_max(H).  The
+// columns of S (stacked states x_1..x_T per unit knot, zero x0) come from
+// rollouts of the parameterized dynamics; H = S' Qbig S + sum_k Om_k' R Om_k
+// with Q, R diagonal.  Power iteration.
+double hessian_lambda_max(const double* A, const double* B, const std::vector<double>& qd,
+                          const std::vector<double>& rd, int n, int m, int T, int p,
+                          const std::vector<int>& idx, const std::vector<double>& w0,
+                          const std::vector<double>& w1) {
+    const int D = m * p;
+    std::vector<double> S((size_t)T * n * D, 0.0), x(n), xn(n);
+    for (int q = 0; q < D; ++q) {
+        const int i = q / p, a = q % p;
+        std::fill(x.begin(), x.end(), 0.0);
+        for (int k = 0; k < T; ++k) {
+            double u = 0.0;
+            if (idx[k] == a) u += w0[k];
+            if (p > 1 && idx[k] + 1 == a) u += w1[k];
+            for (int r = 0; r < n; ++r) {
+                double v = B[(size_t)r * m + i] * u;
+                for (int j = 0; j < n; ++j) v += A[(size_t)r * n + j] * x[j];
+                xn[r] = v;
+            }
+            x.swap(xn);
+            for (int r = 0; r < n; ++r) S[((size_t)k * n + r) * D + q] = x[r];
+        }
+    }
+    std::vector<double> H((size_t)D * D, 0.0);
+    for (int k = 0; k < T; ++k)
+        for (int r = 0; r < n; ++r) {
+            const double* row = &S[((size_t)k * n + r) * D];
+            for (int a = 0; a < D; ++a) {
+                const double va = qd[r] * row[a];
+                if (va == 0.0) continue;
+                for (int b = 0; b < D; ++b) H[(size_t)a * D + b] += va * row[b];
+            }
+        }
+    for (int k = 0; k < T; ++k)
+        for (int i = 0; i < m; ++i) {
+            const int a = i * p + idx[k];
+            H[(size_t)a * D + a] += rd[i] * w0[k] * w0[k];
+            if (p > 1) {
+                const int b = a + 1;
+                H[(size_t)b * D + b] += rd[i] * w1[k] * w1[k];
+                H[(size_t)a * D + b] += rd[i] * w0[k] * w1[k];
+                H[(size_t)b * D + a] += rd[i] * w0[k] * w1[k];
+            }
+        }
+    std::vector<double> v(D, 1.0), hv(D);
+    double lam = 0.0;
+    for (int it = 0; it < 500; ++it) {
+        double nrm = 0.0;
+        for (int a = 0; a < D; ++a) {
+            double t = 0.0;
+            for (int b = 0; b < D; ++b) t += H[(size_t)a * D + b] * v[b];
+            hv[a] = t;
+            nrm += t * t;
+        }
+        nrm = std::sqrt(nrm);
+        if (nrm == 0.0) return 0.0;
+        double vn = 0.0;
+        for (int a = 0; a < D; ++a) vn += v[a] * v[a];
+        const double next = nrm / std::sqrt(vn);
+        for (int a = 0; a < D; ++a) v[a] = hv[a] / nrm;
+        if (std::fabs(next - lam) <= 1e-12 * next) {
+            lam = next;
+            break;
+        }
+        lam = next;
+    }
+    return lam;
 }
 
 empc_status run_generations(empc_handle h, int G) {
@@ -272,6 +398,9 @@ void free_handle(empc_handle h) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->stage) cudaFreeHost(h->stage);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -406,8 +535,10 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     if (cfg.gate < 0 || cfg.gate > 2) return fail(nullptr, EMPC_EINVAL, "bad gate mode");
     if (cfg.precision != EMPC_FP32)
         return fail(nullptr, EMPC_EUNSUPPORTED, "only FP32 precision is built");
-    if (cfg.refine_steps != 0)
-        return fail(nullptr, EMPC_EUNSUPPORTED, "refinement is not built");
+    if (cfg.refine_steps < 0 || cfg.ckpt_every < 0 || !(cfg.refine_lr >= 0.0f))
+        return fail(nullptr, EMPC_EINVAL, "need refine_steps >= 0, ckpt_every >= 0, refine_lr >= 0");
+    if (cfg.refine_steps > 0 && n > 64)
+        return fail(nullptr, EMPC_EUNSUPPORTED, "refinement needs n <= 64");
     if (!finite_all(A, (size_t)n * n) || !finite_all(B, (size_t)n * m) ||
         !finite_all(Q, (size_t)n * n) || !finite_all(R, (size_t)m * m) ||
         !finite_all(bounds, (size_t)m * 2))
@@ -453,6 +584,11 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     } while (0)
     EMPC_TRY(cudaStreamCreate(&h->own_stream));
     h->stream = h->own_stream;
+    EMPC_TRY(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+    EMPC_TRY(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    EMPC_TRY(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    h->ce = cfg.ckpt_every > 0 ? std::min(cfg.ckpt_every, horizon)
+                               : std::max(1, (int)std::ceil(std::sqrt((double)horizon)));
 
     // host-side staging of the model in FP32
     std::vector<float> Dm((size_t)n * n), BT((size_t)m * n), qd(n), rd(m), lo(m), hi(m);
@@ -485,6 +621,17 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     for (int a = 0; a < knots; ++a) {
         gram[a] = (float)Wd[a];
         gram[knots + a] = (float)Wo[a];
+    }
+    if (cfg.refine_steps > 0) {
+        if (cfg.refine_lr > 0.0f) {
+            h->eta = cfg.refine_lr;
+        } else {
+            std::vector<double> qdd(n), rdd(m);
+            for (int i = 0; i < n; ++i) qdd[i] = Q[(size_t)i * n + i];
+            for (int i = 0; i < m; ++i) rdd[i] = R[(size_t)i * m + i];
+            const double lmax = hessian_lambda_max(A, B, qdd, rdd, n, m, horizon, knots, idx, w0, w1);
+            h->eta = lmax > 0.0 ? (float)(1.0 / (2.0 * lmax)) : 0.0f;
+        }
     }
 
     const size_t D = (size_t)h->D;
@@ -525,6 +672,22 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(cudaStreamSynchronize(st));
 #undef EMPC_TRY
     empc_status s = autotune(h);
+    if (s == EMPC_OK && h->n <= 64) {
+        // adjoint kernel shape: 1 candidate per lane, the most warps per CTA
+        // whose shared memory fits
+        h->grad_cands = 1;
+        h->grad_wpc = 0;
+        for (int wpc : {4, 2, 1}) {
+            const size_t need = empc::grad_smem_bytes(h->shape.nx, empc::warp_nrg(h->shape.nx), 1,
+                                                      wpc, n, m, knots, horizon, h->ce);
+            if (need <= 227u * 1024u) {
+                h->grad_wpc = wpc;
+                break;
+            }
+        }
+        if (h->grad_wpc == 0 && cfg.refine_steps > 0)
+            s = fail(h, EMPC_EUNSUPPORTED, "adjoint checkpoints do not fit in shared memory");
+    }
     if (s != EMPC_OK) {
         g_thread_error = h->err;
         free_handle(h);
@@ -599,6 +762,28 @@ empc_status empc_evaluate(empc_handle h, const float* dev_x0, const float* dev_g
     return EMPC_OK;
 }
 
+empc_status empc_grad(empc_handle h, const float* dev_x0, const float* dev_goal,
+                      const float* dev_pop, int count, float* dev_grad, float* dev_cost) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!dev_x0 || !dev_goal || !dev_pop || (!dev_grad && !dev_cost))
+        return fail(h, EMPC_EINVAL, "NULL device pointer");
+    if (count < 0) return fail(h, EMPC_EINVAL, "count must be >= 0");
+    if (h->n > 64) return fail(h, EMPC_EUNSUPPORTED, "the adjoint kernel needs n <= 64");
+    if (count == 0) return EMPC_OK;
+    empc::GradArgs g = grad_args(h);
+    g.x0 = dev_x0;
+    g.goal = dev_goal;
+    g.pop_in = dev_pop;
+    g.ld_in = count;
+    g.count = count;
+    g.grad = dev_grad;
+    g.ld_grad = count;
+    g.cost = dev_cost;
+    g.steps = 0;
+    EMPC_CUDA(h, empc::launch_grad(g, h->shape.nx, h->grad_cands, h->grad_wpc, h->stream));
+    return EMPC_OK;
+}
+
 empc_status empc_get_state(empc_handle h, float* dev_pop, float* dev_cost, int* dev_elite) {
     if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
     if (!h->has_pop) return fail(h, EMPC_ESTATE, "no population yet (solve first)");
@@ -661,7 +846,8 @@ empc_status empc_get_info(empc_handle h, empc_info* info) {
     const int ptile = empc::rollout_cands_per_cta(h->shape, h->n);
     info->ctas = (h->P + ptile - 1) / ptile;
     info->tuned_us = h->tuned_us;
-    info->refine_lr = h->cfg.refine_lr;
+    info->refine_lr = h->eta;
+    info->ckpt_every = h->ce;
     return EMPC_OK;
 }
 

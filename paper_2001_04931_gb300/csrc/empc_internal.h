@@ -43,10 +43,57 @@ struct RolloutArgs {
     const uint32_t* gen;  // device generation counter
     float sigma;
     int pc256, pm256, gate;
-    // optional checkpoint output for the adjoint (may be null)
-    float* ckpt;   // [T/ckpt_every + 1][n][P]
-    int ckpt_every;
+    int cand_begin;  // first candidate this launch covers (later ones up to P)
+    int pdl;         // launch with programmatic stream serialization
 };
+
+// Launch `kern` with an optional programmatic-stream-serialization attribute
+// (programmatic dependent launch on the previous kernel of the stream).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t st, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Adjoint-gradient / refinement kernel arguments (grad.cu).
+struct GradArgs {
+    const float* D;
+    const float* BT;
+    const float* qdiag;
+    const float* rdiag;
+    const float* gram;
+    const KnotStep* ktab;
+    const float* x0;
+    const float* goal;
+    const float* umin;
+    const float* umax;
+    int n, m, T, p;
+    const float* pop_in;  // SoA knots, stride ld_in
+    int ld_in;
+    const int* index;     // candidate c reads column index[c] (null: column c)
+    int count;            // candidates processed
+    float* grad;          // SoA gradient output, stride ld_grad (steps == 0)
+    int ld_grad;
+    float* cost;          // cost[count] of the final knots (may be null)
+    float* pop_out;       // refined knots, column c, stride ld_out (steps > 0)
+    int ld_out;
+    int ce;               // checkpoint interval
+    int steps;            // projected-gradient steps (0: gradient only)
+    float eta;            // step size
+};
+
+cudaError_t launch_grad(const GradArgs& a, int nx, int cands, int wpc, cudaStream_t st);
+size_t grad_smem_bytes(int nx, int nrg, int cands, int wpc, int n, int m, int p, int T, int ce);
 
 // Rollout tile.  kind 0 (block): ceil(n/rows) threads per candidate group,
 // `groups` candidate groups per CTA, one block barrier per step.  kind 1
@@ -82,7 +129,8 @@ int warp_nrg(int nx);
 // Writes elite_idx[E], elite_cost[E], best_knots[m p] and increments *gen.
 cudaError_t launch_select(const float* cost, int P, int E, const float* pop, int D,
                           int* elite_idx, float* elite_cost, float* best_knots,
-                          float* best_cost, uint32_t* gen, int* status, cudaStream_t st);
+                          float* best_cost, uint32_t* gen, int* status, cudaStream_t st,
+                          bool pdl = false);
 
 // Record a failure message for empc_last_error(NULL) on this thread; returns s.
 int set_thread_error(int s, const char* msg);

@@ -46,11 +46,11 @@ __global__ void rollout_block_kernel(const RolloutArgs a) {
     float* BTs = smem + L.off_bt;
     KnotStep* ks = reinterpret_cast<KnotStep*>(smem + L.off_k);
     int* par = reinterpret_cast<int*>(smem + L.off_par);
-    const int c0 = blockIdx.x * ptile;
+    const int c0 = a.cand_begin + blockIdx.x * ptile;
     const int tid = threadIdx.x;
     const int rg = tid % nrg;
     const int cg = tid / nrg;
-    const uint32_t gen = a.gen ? *a.gen : 0u;
+    pdl_launch_dependents();
 
     for (int i = tid; i < 2 * NX * xs; i += blockDim.x) {
         const int k = (i / xs) % NX;
@@ -61,10 +61,11 @@ __global__ void rollout_block_kernel(const RolloutArgs a) {
         BTs[i] = row < n ? a.BT[col * n + row] : 0.0f;
     }
     for (int k = tid; k < a.T; k += blockDim.x) ks[k] = a.ktab[k];
-    fill_knots<false>(a, Us, xs, par, c0, ptile, gen, tid, blockDim.x);  // ends with a barrier
-
     float d[R][NX], qd[R], gl[R], xo[R][C], jsum[C];
     load_rows<NX, R, C>(a, rg * R, d, qd, gl, xo);
+    pdl_wait_primary();
+    const uint32_t gen = a.gen ? *a.gen : 0u;
+    fill_knots<false>(a, Us, xs, par, c0, ptile, gen, tid, blockDim.x);  // ends with a barrier
     horizon_loop<NX, R, C, false>(a, d, X, NX, xs, BTs, NX, Us, ks, rg * R, cg * C, xo, qd, gl,
                                   jsum);
 
@@ -99,9 +100,9 @@ cudaError_t launch_shape(const RolloutArgs& a, int groups, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         smem_cap = (int)smem;
     }
-    const int grid = (a.P + ptile - 1) / ptile;
-    kern<<<grid, nrg * groups, smem, st>>>(a);
-    return cudaGetLastError();
+    const int grid = (a.P - a.cand_begin + ptile - 1) / ptile;
+    if (grid <= 0) return cudaSuccess;
+    return launch_kernel(kern, dim3(grid), dim3(nrg * groups), smem, st, a.pdl != 0, a);
 }
 
 template <int NX, int R, int C>
@@ -156,7 +157,7 @@ int rollout_shapes(int n, TileShape* out, int cap) {
         if (k < cap) out[k] = s;
         ++k;
     };
-    if (nx <= 64) {  // warp-synchronous family first
+    if (nx <= 64) {  // warp-synchronous family
         const int nrg = warp_nrg(nx);
         const int rows = (nx + nrg - 1) / nrg;
         for (int cands : {2, 1, 4})

@@ -41,6 +41,17 @@ __device__ __forceinline__ void store_vec(float* p, const float (&v)[C]) {
 
 __host__ __device__ __forceinline__ int round_up(int v, int to) { return (v + to - 1) / to * to; }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// CTAs (they run their prologue, then wait), and wait here until the previous
+// kernel has completed and its writes are visible.  Both are no-ops for a
+// kernel launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait_primary() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // out[r][c] = sum_i B_d[row0 + r][i] U[i*p + a][col0 + c]  (knot force B_d U_a).
 // BTs holds B_d transposed with leading dimension ldb (rows beyond n zero).
 template <int R, int C>
@@ -60,6 +71,59 @@ __device__ __forceinline__ void knot_force(const float* BTs, int ldb, const floa
 #pragma unroll
             for (int c = 0; c < C; ++c) out[r][c] = fmaf(b, u[c], out[r][c]);
         }
+    }
+}
+
+// Paired FP32 fused multiply-add (fma.rn.f32x2, sm_100 and later): two
+// independent IEEE round-to-nearest FMAs in one instruction.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// Pair-interleaved state tile: row k of column col lives at
+// ((k / 2) * xs + col) * 2 + (k & 1), so one vector load returns rows
+// (k, k+1) for consecutive columns.
+__host__ __device__ __forceinline__ int pair_index(int k, int col, int xs) {
+    return ((k >> 1) * xs + col) * 2 + (k & 1);
+}
+
+// Four partial sums of sum_k d[r][k] X[k][c] in two paired accumulators:
+// accA[r][c] = {sum over k = 0 mod 4, sum over k = 1 mod 4},
+// accB[r][c] = {sum over k = 2 mod 4, sum over k = 3 mod 4}, one paired FMA
+// per (row, candidate, k pair).  Four independent chains per output keep the
+// FMA pipe fed; the order is fixed, the same for every candidate.
+template <int NX, int R, int C>
+__device__ __forceinline__ void state_product_pairs(const float2 (&d2)[R][NX / 2],
+                                                    const float* Xp, int xs,
+                                                    float2 (&accA)[R][C],
+                                                    float2 (&accB)[R][C]) {
+#pragma unroll
+    for (int kp = 0; kp < NX / 2; ++kp) {
+        float2 xv[C];
+        const float* src = Xp + kp * xs * 2;
+        if constexpr (C == 1) {
+            xv[0] = *reinterpret_cast<const float2*>(src);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; c += 2) {
+                const float4 t = *reinterpret_cast<const float4*>(src + 2 * c);
+                xv[c] = make_float2(t.x, t.y);
+                xv[c + 1] = make_float2(t.z, t.w);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (kp & 1) accB[r][c] = fma2(d2[r][kp], xv[c], accB[r][c]);
+                else accA[r][c] = fma2(d2[r][kp], xv[c], accA[r][c]);
+            }
     }
 }
 
@@ -147,10 +211,20 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
                 if (s2 < 0) {
 #pragma unroll
                     for (int w = 0; w < 4; ++w)
-                        if (q0 + w < D) v[w] = a.pop_in[(size_t)(q0 + w) * a.P + s1];
+                        if (q0 + w < D) v[w] = __ldg(a.pop_in + (size_t)(q0 + w) * a.P + s1);
                 } else {
                     const uint32_t cross =
                         draw(a.seed, (uint32_t)c, gen, kDrawCross, (uint32_t)(quad >> 2)).w[quad & 3];
+                    // issue the parent-knot gathers before the remaining draws
+                    float mate[4];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int q = q0 + w;
+                        const uint32_t cb = (cross >> (8 * w)) & 0xFFu;
+                        mate[w] = q < D ? __ldg(a.pop_in + (size_t)q * a.P +
+                                                (cb < (uint32_t)a.pc256 ? s2 : s1))
+                                        : 0.0f;
+                    }
                     Words4 gw;
                     uint32_t gate_blk = 0xFFFFFFFFu;
                     float z[4];
@@ -160,10 +234,6 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
                         const int q = q0 + w;
                         if (q >= D) continue;
                         const int i = q / a.p;
-                        const uint32_t cb = (cross >> (8 * w)) & 0xFFu;
-                        const float mate = (cb < (uint32_t)a.pc256)
-                                               ? a.pop_in[(size_t)q * a.P + s2]
-                                               : a.pop_in[(size_t)q * a.P + s1];
                         bool mut = true;
                         if (a.gate != 2) {
                             const uint32_t gb = (a.gate == 0) ? (uint32_t)i : (uint32_t)q;
@@ -174,7 +244,7 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
                             mut = ((gw.w[(gb >> 2) & 3u] >> (8u * (gb & 3u))) & 0xFFu) <
                                   (uint32_t)a.pm256;
                         }
-                        float val = mate;
+                        float val = mate[w];
                         if (mut) {
                             if (!have_z) {
                                 const Words4 nz =
@@ -183,7 +253,7 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
                                 gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
                                 have_z = true;
                             }
-                            val = __fmaf_rn(a.sigma, z[w], mate);
+                            val = __fmaf_rn(a.sigma, z[w], mate[w]);
                         }
                         v[w] = clamp_to(val, a.umin[i], a.umax[i]);
                     }
@@ -205,7 +275,8 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
 // Input cost sum_k u_k' R u_k of one candidate restricted to inputs
 // i0, i0 + istep, ..., in closed form through the tridiagonal Gram matrix of
 // the knot weights (W_aa = gram[a], W_a,a+1 = gram[p + a]).
-__device__ __forceinline__ float input_cost_part(const RolloutArgs& a, const float* Us, int xs,
+template <class Args>
+__device__ __forceinline__ float input_cost_part(const Args& a, const float* Us, int xs,
                                                  int col, int i0, int istep) {
     const int p = a.p;
     float Ju = 0.0f;

@@ -32,13 +32,94 @@ int warp_nrg(int nx) {
 
 namespace {
 
-template <int NX, int NRG, int C>
+// Row groups per candidate group (warp_nrg as a compile-time function).
+__host__ __device__ constexpr int nrg_of(int nx) {
+    return nx == 4 ? 2 : nx == 8 ? 4 : nx <= 24 ? 8 : nx <= 48 ? 16 : 32;
+}
+
+// The horizon loop of rollout_common.cuh's horizon_loop on the
+// pair-interleaved state tile, with paired FMAs and four partial sums per
+// output (state_product_pairs).
+template <int NX, int R, int C>
+__device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
+                                                   const float2 (&d2)[R][NX / 2], float* X,
+                                                   int xrows, int xs, const float* BTs, int ldb,
+                                                   const float* Us, const KnotStep* ks,
+                                                   int row0, int col0, float (&xo)[R][C],
+                                                   const float (&qd)[R], const float (&gl)[R],
+                                                   float (&jsum)[C]) {
+    float bua[R][C], bub[R][C];
+    int seg = -1;
+    float jtot[C], jblk[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) jtot[c] = jblk[c] = 0.0f;
+    int buf = 0;
+    for (int k = 0; k < a.T; ++k) {
+        const KnotStep st = ks[k];
+        if (st.idx1 != seg) {
+            if (st.idx1 == seg + 1 && seg >= 0) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) bua[r][c] = bub[r][c];
+            } else {
+                knot_force<R, C>(BTs, ldb, Us, xs, a.m, a.p, st.idx1, row0, col0, bua);
+            }
+            if (st.idx1 + 1 < a.p) {
+                knot_force<R, C>(BTs, ldb, Us, xs, a.m, a.p, st.idx1 + 1, row0, col0, bub);
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) bub[r][c] = 0.0f;
+            }
+            seg = st.idx1;
+        }
+        float2 accA[R][C], accB[R][C];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                accA[r][c] = make_float2(fmaf(st.w1, bub[r][c], st.w0 * bua[r][c]), 0.0f);
+                accB[r][c] = make_float2(0.0f, 0.0f);
+            }
+        state_product_pairs<NX, R, C>(d2, X + buf * xrows * xs + 2 * col0, xs, accA, accB);
+        float* Xn = X + (buf ^ 1) * xrows * xs;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float sum = (accA[r][c].x + accB[r][c].x) + (accA[r][c].y + accB[r][c].y);
+                const float xn = xo[r][c] + sum;
+                xo[r][c] = xn;
+                const float e = xn - gl[r];
+                jblk[c] = fmaf(qd[r] * e, e, jblk[c]);
+                Xn[pair_index(row0 + r, col0 + c, xs)] = xn;
+            }
+        }
+        if ((k & 15) == 15) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                jtot[c] += jblk[c];
+                jblk[c] = 0.0f;
+            }
+        }
+        __syncwarp();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) jsum[c] = jtot[c] + jblk[c];
+}
+
+template <int NX, int C>
 __global__ void rollout_warp_kernel(const RolloutArgs a) {
+    constexpr int NRG = nrg_of(NX);
     constexpr int R = (NX + NRG - 1) / NRG;
     constexpr int XR = NRG * R;
     constexpr int CGW = 32 / NRG;
     constexpr int CPW = CGW * C;
     constexpr int XS = (CPW + 3) / 4 * 4;
+    constexpr int KP = NX / 2;
     extern __shared__ __align__(16) float smem[];
     const int m = a.m, p = a.p, T = a.T;
     const int D = m * p;
@@ -51,8 +132,8 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
     float* X = W;
     float* Us = W + 2 * XR * XS;
     int* par = reinterpret_cast<int*>(Us + D * XS);
-    const int c0 = (blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
-    const uint32_t gen = a.gen ? *a.gen : 0u;
+    const int c0 = a.cand_begin + (blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
+    pdl_launch_dependents();
 
     for (int i = threadIdx.x; i < m * XR; i += blockDim.x) {
         const int row = i % XR, col = i / XR;
@@ -62,15 +143,34 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
     __syncthreads();
     if (c0 >= a.P) return;  // no block barrier follows
 
-    for (int i = lane; i < 2 * XR * XS; i += 32) {
-        const int k = (i / XS) % XR;
+    for (int i = lane; i < 2 * XR * XS; i += 32) {  // pair-interleaved rows
+        const int j = i % (XR * XS);
+        const int k = 2 * (j / (2 * XS)) + (j & 1);
         X[i] = (i < XR * XS && k < a.n) ? a.x0[k] : 0.0f;
     }
+    float qd[R], gl[R], xo[R][C], jsum[C];
+    float2 d2[R][KP];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = rg * R + r;
+        const bool ok = row < a.n;
+#pragma unroll
+        for (int kp = 0; kp < KP; ++kp) {
+            const int k = 2 * kp;
+            d2[r][kp] = make_float2((ok && k < a.n) ? a.D[row * a.n + k] : 0.0f,
+                                    (ok && k + 1 < a.n) ? a.D[row * a.n + k + 1] : 0.0f);
+        }
+        qd[r] = ok ? a.qdiag[row] : 0.0f;
+        gl[r] = ok ? a.goal[row] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) xo[r][c] = ok ? a.x0[row] : 0.0f;
+    }
+    // everything above reads only the model; the population, the elites and
+    // the generation counter come from the previous kernels
+    pdl_wait_primary();
+    const uint32_t gen = a.gen ? *a.gen : 0u;
     fill_knots<true>(a, Us, XS, par, c0, CPW, gen, lane, 32);  // ends with a warp barrier
-
-    float d[R][NX], qd[R], gl[R], xo[R][C], jsum[C];
-    load_rows<NX, R, C>(a, rg * R, d, qd, gl, xo);
-    horizon_loop<NX, R, C, true>(a, d, X, XR, XS, BTs, XR, Us, ks, rg * R, cgl * C, xo, qd, gl,
+    horizon_loop_pairs<NX, R, C>(a, d2, X, XR, XS, BTs, XR, Us, ks, rg * R, cgl * C, xo, qd, gl,
                                  jsum);
 
     // each lane adds the input cost of inputs rg, rg + NRG, ...; then a
@@ -87,11 +187,11 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
 
 template <int NX, int C>
 cudaError_t launch_shape(const RolloutArgs& a, int wpc, cudaStream_t st) {
-    constexpr int NRG = NX == 4 ? 2 : NX == 8 ? 4 : NX <= 24 ? 8 : NX <= 48 ? 16 : 32;
+    constexpr int NRG = nrg_of(NX);
     constexpr int CPW = (32 / NRG) * C;
     TileShape s{1, NX, (NX + NRG - 1) / NRG, C, wpc};
     const size_t smem = rollout_smem_bytes(s, a.n, a.m, a.p, a.T);
-    auto kern = rollout_warp_kernel<NX, NRG, C>;
+    auto kern = rollout_warp_kernel<NX, C>;
     static int smem_cap = 48 * 1024;
     if ((int)smem > smem_cap) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -100,16 +200,15 @@ cudaError_t launch_shape(const RolloutArgs& a, int wpc, cudaStream_t st) {
         smem_cap = (int)smem;
     }
     const int per_cta = wpc * CPW;
-    const int grid = (a.P + per_cta - 1) / per_cta;
-    kern<<<grid, 32 * wpc, smem, st>>>(a);
-    return cudaGetLastError();
+    const int grid = (a.P - a.cand_begin + per_cta - 1) / per_cta;
+    if (grid <= 0) return cudaSuccess;
+    return launch_kernel(kern, dim3(grid), dim3(32 * wpc), smem, st, a.pdl != 0, a);
 }
 
 template <int NX, int C>
 int max_threads_of() {
-    constexpr int NRG = NX == 4 ? 2 : NX == 8 ? 4 : NX <= 24 ? 8 : NX <= 48 ? 16 : 32;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, rollout_warp_kernel<NX, NRG, C>) != cudaSuccess) return 0;
+    if (cudaFuncGetAttributes(&fa, rollout_warp_kernel<NX, C>) != cudaSuccess) return 0;
     return fa.maxThreadsPerBlock;
 }
 
@@ -118,11 +217,11 @@ int max_threads_of() {
 }  // namespace
 
 cudaError_t launch_rollout_warp(const RolloutArgs& a, const TileShape& s, cudaStream_t st) {
-#define EMPC_CASE(NXV)                                                   \
-    if (s.nx == NXV) {                                                   \
-        if (s.cands == 1) return launch_shape<NXV, 1>(a, s.groups, st);  \
-        if (s.cands == 2) return launch_shape<NXV, 2>(a, s.groups, st);  \
-        if (s.cands == 4) return launch_shape<NXV, 4>(a, s.groups, st);  \
+#define EMPC_CASE(NXV)                                                       \
+    if (s.nx == NXV) {                                                       \
+        if (s.cands == 1) return launch_shape<NXV, 1>(a, s.groups, st);      \
+        if (s.cands == 2) return launch_shape<NXV, 2>(a, s.groups, st);      \
+        if (s.cands == 4) return launch_shape<NXV, 4>(a, s.groups, st);      \
     }
     EMPC_WARP_NX_CASES(EMPC_CASE)
 #undef EMPC_CASE
@@ -130,11 +229,11 @@ cudaError_t launch_rollout_warp(const RolloutArgs& a, const TileShape& s, cudaSt
 }
 
 int warp_max_threads(const TileShape& s) {
-#define EMPC_CASE(NXV)                                        \
-    if (s.nx == NXV) {                                        \
-        if (s.cands == 1) return max_threads_of<NXV, 1>();    \
-        if (s.cands == 2) return max_threads_of<NXV, 2>();    \
-        if (s.cands == 4) return max_threads_of<NXV, 4>();    \
+#define EMPC_CASE(NXV)                                              \
+    if (s.nx == NXV) {                                              \
+        if (s.cands == 1) return max_threads_of<NXV, 1>();          \
+        if (s.cands == 2) return max_threads_of<NXV, 2>();          \
+        if (s.cands == 4) return max_threads_of<NXV, 4>();          \
     }
     EMPC_WARP_NX_CASES(EMPC_CASE)
 #undef EMPC_CASE

@@ -12,6 +12,11 @@
 //      compares, E <= 2048) and scatter to rank order;
 //   5. copy the best candidate's knots and cost out and bump the generation
 //      counter that keys the next generation's draws.
+// Fast path (steps 2-3 replaced): slots 0..E-1 always hold E candidates
+// (after a warm start, the previous elites re-evaluated), so the E-th
+// smallest (key, index) pair is at most K*, the largest pair among those
+// slots.  When few candidates lie at or below K* they are compacted
+// directly and ranked by counting; otherwise the radix select runs.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -57,6 +62,22 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return r;
 }
 
+// Copy the best candidate's knots and cost out; bump the generation counter.
+__device__ __forceinline__ void finish_select(const float* __restrict__ cost, int P,
+                                              const float* __restrict__ pop, int D,
+                                              float* __restrict__ best_knots,
+                                              float* __restrict__ best_cost,
+                                              uint32_t* __restrict__ gen,
+                                              int* __restrict__ status, int best) {
+    for (int q = threadIdx.x; q < D; q += blockDim.x) best_knots[q] = pop[(size_t)q * P + best];
+    if (threadIdx.x == 0) {
+        const float bc = cost[best];
+        *best_cost = bc;
+        if (gen) *gen += 1u;
+        if (status && !(bc < __int_as_float(0x7f800000))) atomicOr(status, 1);
+    }
+}
+
 template <int KPT>
 __global__ void __launch_bounds__(kSelThreads) select_kernel(
     const float* __restrict__ cost, int P, int E, const float* __restrict__ pop, int D,
@@ -66,14 +87,86 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t s_digit, s_rem;
     __shared__ int s_best;
+    __shared__ uint32_t s_count;
+    __shared__ unsigned long long s_kstar;
+    __shared__ unsigned long long s_red64[32];
     __shared__ unsigned long long sel[kMaxElite];
 
     const int tid = threadIdx.x;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     uint32_t key[KPT];
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         const int idx = tid * KPT + j;
         key[j] = idx < P ? order_key(cost[idx]) : 0xFFFFFFFFu;
+    }
+
+    // ---- fast path: bound from slots 0..E-1
+    const int lane = tid & 31, warp = tid >> 5;
+    {
+        unsigned long long kmax = 0ull;
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const int idx = tid * KPT + j;
+            if (idx < E) kmax = max(kmax, ((unsigned long long)key[j] << 32) | (uint32_t)idx);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        if (lane == 0) s_red64[warp] = kmax;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long v = s_red64[lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) {
+                s_kstar = v;
+                s_count = 0;
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long kstar = s_kstar;
+    uint32_t nbelow = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        const int idx = tid * KPT + j;
+        nbelow += (idx < P && (((unsigned long long)key[j] << 32) | (uint32_t)idx) <= kstar);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nbelow += __shfl_xor_sync(0xffffffffu, nbelow, o);
+    if (lane == 0) warp_tot[warp] = nbelow;
+    __syncthreads();
+    uint32_t L = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) L += warp_tot[w];
+    const uint32_t cap = (uint32_t)min(kMaxElite, max(4 * E, 512));
+    if (L <= cap) {
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const int idx = tid * KPT + j;
+            const unsigned long long k64 = ((unsigned long long)key[j] << 32) | (uint32_t)idx;
+            const bool take = idx < P && k64 <= kstar;
+            const uint32_t ball = __ballot_sync(0xffffffffu, take);
+            uint32_t base = 0;
+            if (lane == 0 && ball) base = atomicAdd(&s_count, (uint32_t)__popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) sel[base + __popc(ball & ((1u << lane) - 1u))] = k64;
+        }
+        __syncthreads();
+        for (int e = tid; e < (int)L; e += blockDim.x) {
+            const unsigned long long mine = sel[e];
+            int rank = 0;
+            for (int f = 0; f < (int)L; ++f) rank += sel[f] < mine;
+            if (rank < E) {
+                const int idx = (int)(mine & 0xFFFFFFFFull);
+                elite_idx[rank] = idx;
+                elite_cost[rank] = cost[idx];
+                if (rank == 0) s_best = idx;
+            }
+        }
+        __syncthreads();
+        finish_select(cost, P, pop, D, best_knots, best_cost, gen, status, s_best);
+        return;
     }
 
     // ---- radix select of the E-th smallest key
@@ -166,35 +259,28 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(
         if (rank == 0) s_best = idx;
     }
     __syncthreads();
-    const int best = s_best;
-    for (int q = tid; q < D; q += blockDim.x) best_knots[q] = pop[(size_t)q * P + best];
-    if (tid == 0) {
-        const float bc = cost[best];
-        *best_cost = bc;
-        if (gen) *gen += 1u;
-        if (status && !(bc < __int_as_float(0x7f800000))) atomicOr(status, 1);
-    }
+    finish_select(cost, P, pop, D, best_knots, best_cost, gen, status, s_best);
 }
 
 }  // namespace
 
 cudaError_t launch_select(const float* cost, int P, int E, const float* pop, int D,
                           int* elite_idx, float* elite_cost, float* best_knots,
-                          float* best_cost, uint32_t* gen, int* status, cudaStream_t st) {
+                          float* best_cost, uint32_t* gen, int* status, cudaStream_t st,
+                          bool pdl) {
     if (P <= 0 || E <= 0 || E > P || E > kMaxElite) return cudaErrorInvalidValue;
     const int kpt = (P + kSelThreads - 1) / kSelThreads;
 #define EMPC_SEL(K)                                                                      \
-    select_kernel<K><<<1, kSelThreads, 0, st>>>(cost, P, E, pop, D, elite_idx, elite_cost, \
-                                                best_knots, best_cost, gen, status)
+    return launch_kernel(select_kernel<K>, dim3(1), dim3(kSelThreads), 0, st, pdl, cost, P, E, \
+                         pop, D, elite_idx, elite_cost, best_knots, best_cost, gen, status)
     if (kpt <= 1) EMPC_SEL(1);
-    else if (kpt <= 2) EMPC_SEL(2);
-    else if (kpt <= 4) EMPC_SEL(4);
-    else if (kpt <= 8) EMPC_SEL(8);
-    else if (kpt <= 16) EMPC_SEL(16);
-    else if (kpt <= 32) EMPC_SEL(32);
-    else return cudaErrorInvalidValue;
+    if (kpt <= 2) EMPC_SEL(2);
+    if (kpt <= 4) EMPC_SEL(4);
+    if (kpt <= 8) EMPC_SEL(8);
+    if (kpt <= 16) EMPC_SEL(16);
+    if (kpt <= 32) EMPC_SEL(32);
 #undef EMPC_SEL
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace empc

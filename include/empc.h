@@ -223,6 +223,68 @@ void empc_destroy(empc_handle h);
  * for calls without a handle when h is NULL).  Owned by the library. */
 const char* empc_last_error(empc_handle h);
 
+/* ---------------------------------------------------------------------- */
+/* Batched EMPC: many independent problems in one persistent launch (no    */
+/* counterpart in the paper).                                              */
+/* ---------------------------------------------------------------------- */
+typedef struct empc_batch_s* empc_batch;
+
+/* One problem of a batch: the empc_create arguments plus its start, goal and
+ * breeding seed.  All host FP64 except seed/sigma; n <= 64.  elite 0 =
+ * max(1, pop/16); sigma 0 = the batch config's sigma. */
+typedef struct {
+    const double* A;
+    const double* B;
+    const double* Q;
+    const double* R;
+    const double* bounds;
+    const double* x0;
+    const double* x_goal;
+    int n, m, horizon, knots, pop, elite;
+    uint64_t seed;
+    float sigma;
+} empc_problem_desc;
+
+typedef struct {
+    int count, total_knots;
+    int ctas, warps_per_cta, cands_per_lane, items_per_generation;
+    double state_steps_per_generation;  /* sum over problems of pop * horizon */
+    float tuned_us;                     /* autotuned cold generation of the whole batch */
+} empc_batch_info;
+
+/*
+ * empc_batch_create - upload `count` problems (copied; caller keeps
+ * ownership) into one device arena and autotune the persistent launch shape
+ * (warps per CTA, candidates per lane) on a cold generation.  cfg supplies
+ * the shared breeding parameters (p_cross_256, p_mutate_256, gate, sigma
+ * default); cfg.tile > 0 forces launch shape tile-1.  FP32, no refinement.
+ */
+empc_status empc_batch_create(const empc_problem_desc* probs, int count, const empc_config* cfg,
+                              empc_batch* out);
+
+/*
+ * empc_batch_solve - `generations` generations of every problem in one
+ * persistent kernel launch (replayed from a cached CUDA graph).  Outputs
+ * (host): best_knots, the problems' best knot vectors concatenated in order
+ * ([m_i * p_i] each), and best_costs [count].  Populations persist (warm
+ * start); empc_batch_reset makes the next generation cold.  Device waits are
+ * bounded; if one runs out the call returns EMPC_ETIMEOUT and the next solve
+ * starts cold.  EMPC_ENONFINITE if a problem's best cost is not finite.
+ */
+empc_status empc_batch_solve(empc_batch b, int generations, float* best_knots, float* best_costs);
+empc_status empc_batch_reset(empc_batch b);
+/* Current population [m*p][pop], costs [pop] and elites [E] of problem
+ * `index` into device buffers (any may be NULL); synchronous. */
+empc_status empc_batch_get_state(empc_batch b, int index, float* dev_pop, float* dev_cost,
+                                 int* dev_elite);
+empc_status empc_batch_get_info(empc_batch b, empc_batch_info* info);
+/* Failure injection for tests: problem `problem` (-1: none) never publishes
+ * its selected generation, so every wait on it runs out after timeout_s
+ * seconds (also the wait limit used from now on). */
+empc_status empc_batch_inject_stall(empc_batch b, int problem, double timeout_s);
+void empc_batch_destroy(empc_batch b);
+const char* empc_batch_last_error(empc_batch b);
+
 /*
  * empc_discretize_zoh - zero-order-hold discretization of x' = Ac x + Bc u
  * over dt (Sec. III-A, "matrix exponential"): [[Ad, Bd], [0, I]] =

@@ -46,6 +46,24 @@ class empc_info(ctypes.Structure):
                 ("tile_kind", ctypes.c_int), ("ckpt_every", ctypes.c_int)]
 
 
+class empc_problem_desc(ctypes.Structure):
+    _fields_ = [("A", ctypes.POINTER(ctypes.c_double)), ("B", ctypes.POINTER(ctypes.c_double)),
+                ("Q", ctypes.POINTER(ctypes.c_double)), ("R", ctypes.POINTER(ctypes.c_double)),
+                ("bounds", ctypes.POINTER(ctypes.c_double)),
+                ("x0", ctypes.POINTER(ctypes.c_double)),
+                ("x_goal", ctypes.POINTER(ctypes.c_double)), ("n", ctypes.c_int),
+                ("m", ctypes.c_int), ("horizon", ctypes.c_int), ("knots", ctypes.c_int),
+                ("pop", ctypes.c_int), ("elite", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("sigma", ctypes.c_float)]
+
+
+class empc_batch_info(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("total_knots", ctypes.c_int), ("ctas", ctypes.c_int),
+                ("warps_per_cta", ctypes.c_int), ("cands_per_lane", ctypes.c_int),
+                ("items_per_generation", ctypes.c_int),
+                ("state_steps_per_generation", ctypes.c_double), ("tuned_us", ctypes.c_float)]
+
+
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
 _vp = ctypes.c_void_p
@@ -73,6 +91,15 @@ _SIGNATURES = {
     "empc_measure_fp32_peak": (_i, [_dp]),
     "empc_evaluate_noalloc": (_i, [_dp, _dp, _dp, _dp, _i, _i, _i, _i, _vp, _vp, _vp, _i,
                                   _vp, _vp]),
+    "empc_batch_create": (_i, [ctypes.POINTER(empc_problem_desc), _i,
+                               ctypes.POINTER(empc_config), ctypes.POINTER(_h)]),
+    "empc_batch_solve": (_i, [_h, _i, _fp, _fp]),
+    "empc_batch_reset": (_i, [_h]),
+    "empc_batch_get_state": (_i, [_h, _i, _vp, _vp, _vp]),
+    "empc_batch_get_info": (_i, [_h, ctypes.POINTER(empc_batch_info)]),
+    "empc_batch_inject_stall": (_i, [_h, _i, ctypes.c_double]),
+    "empc_batch_destroy": (None, [_h]),
+    "empc_batch_last_error": (ctypes.c_char_p, [_h]),
 }
 
 
@@ -234,3 +261,78 @@ class Problem:
 
     def set_stream(self, stream):
         check(_lib.empc_set_stream(self.handle, stream), self.handle)
+
+
+def _bcheck(status, batch):
+    if status != EMPC_OK:
+        msg = _lib.empc_batch_last_error(batch)
+        raise EmpcError(status, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many independent problems solved in one persistent launch (empc_batch_*).
+
+    `problems` is a list of dicts with keys A, B, Q, R, bounds, x0, x_goal,
+    horizon, knots, pop and optionally elite, seed, sigma."""
+
+    def __init__(self, problems, config=None, **cfg):
+        self._keep = []
+        descs = (empc_problem_desc * len(problems))()
+        self.dims = []
+        for d, pr in zip(descs, problems):
+            arrs = {k: _d(pr[k]) for k in ("A", "B", "Q", "R", "bounds", "x0", "x_goal")}
+            self._keep.append(arrs)
+            for k, v in arrs.items():
+                setattr(d, k, _ptr(v))
+            n, m = arrs["B"].shape
+            d.n, d.m = n, m
+            d.horizon, d.knots, d.pop = int(pr["horizon"]), int(pr["knots"]), int(pr["pop"])
+            d.elite = int(pr.get("elite", 0))
+            d.seed = int(pr.get("seed", 0))
+            d.sigma = float(pr.get("sigma", 0.0))
+            self.dims.append((n, m, d.horizon, d.knots, d.pop))
+        c = config if config is not None else default_config(**cfg)
+        h = _h()
+        _bcheck(_lib.empc_batch_create(descs, len(problems), ctypes.byref(c), ctypes.byref(h)),
+                None)
+        self.handle = h
+        self.total_knots = sum(m * p for _, m, _, p, _ in self.dims)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.empc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = empc_batch_info()
+        _bcheck(_lib.empc_batch_get_info(self.handle, ctypes.byref(inf)), self.handle)
+        return inf
+
+    def solve(self, generations):
+        """(list of best knot vectors, costs[count]) after `generations`."""
+        knots = np.zeros(self.total_knots, np.float32)
+        costs = np.zeros(len(self.dims), np.float32)
+        _bcheck(_lib.empc_batch_solve(self.handle, int(generations), knots.ctypes.data_as(_fp),
+                                      costs.ctypes.data_as(_fp)), self.handle)
+        out, at = [], 0
+        for _, m, _, p, _ in self.dims:
+            out.append(knots[at:at + m * p].copy())
+            at += m * p
+        return out, costs
+
+    def reset(self):
+        _bcheck(_lib.empc_batch_reset(self.handle), self.handle)
+
+    def get_state(self, index, pop=None, cost=None, elite=None):
+        _bcheck(_lib.empc_batch_get_state(self.handle, int(index), _dev(pop), _dev(cost),
+                                          _dev(elite)), self.handle)
+
+    def inject_stall(self, problem, timeout_s):
+        _bcheck(_lib.empc_batch_inject_stall(self.handle, int(problem), float(timeout_s)),
+                self.handle)

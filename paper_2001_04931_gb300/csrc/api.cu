@@ -15,6 +15,7 @@
 
 #include "../../include/empc.h"
 #include "empc_internal.h"
+#include "host_tables.h"
 
 using empc::KnotStep;
 using empc::RolloutArgs;
@@ -91,38 +92,6 @@ empc_status cuda_fail(empc_handle h, cudaError_t e, const char* where) {
         cudaError_t e_ = (call);                                    \
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
     } while (0)
-
-bool finite_all(const double* v, size_t k) {
-    for (size_t i = 0; i < k; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
-}
-
-// Knot table of Sec. IV-C in exact integers: idx1 = min(floor(k (p-1) /
-// (T-1)), p-2), c = (k (p-1) - idx1 (T-1)) / (T-1).  The weights are exact
-// rationals rounded once to FP32.  p == 1 or T == 1: constant input.
-void make_knot_table(int T, int p, std::vector<KnotStep>& ks, std::vector<double>& w0,
-                     std::vector<double>& w1, std::vector<int>& idx) {
-    ks.resize(T);
-    w0.resize(T);
-    w1.resize(T);
-    idx.resize(T);
-    const long den = T > 1 ? T - 1 : 1;
-    for (int k = 0; k < T; ++k) {
-        long a = 0, num = 0;
-        if (p > 1 && T > 1) {
-            a = std::min<long>((long)k * (p - 1) / den, p - 2);
-            num = (long)k * (p - 1) - a * den;
-        }
-        idx[k] = (int)a;
-        w1[k] = (double)num / (double)den;
-        w0[k] = (double)(den - num) / (double)den;
-        ks[k].idx1 = (int)a;
-        ks[k].w0 = (float)w0[k];
-        ks[k].w1 = (float)w1[k];
-        ks[k].pad = 0;
-    }
-}
 
 template <typename T>
 cudaError_t dev_alloc(T** p, size_t count) {
@@ -516,12 +485,12 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
                         const empc_config* cfg_in, empc_handle* out) {
     if (!out) return fail(nullptr, EMPC_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!A || !B || !Q || !R || !bounds) return fail(nullptr, EMPC_EINVAL, "NULL model pointer");
-    if (n < 1 || n > 128 || m < 1 || m > 128)
-        return fail(nullptr, EMPC_EINVAL, "need 1 <= n <= 128 and 1 <= m <= 128");
-    if (horizon < 1 || knots < 1 || knots > horizon)
-        return fail(nullptr, EMPC_EINVAL, "need horizon >= 1 and 1 <= knots <= horizon");
-    if (pop < 1 || pop > 32768) return fail(nullptr, EMPC_EINVAL, "need 1 <= pop <= 32768");
+    {
+        std::string msg;
+        const empc_status vs =
+            empc::validate_problem(A, B, Q, R, bounds, n, m, horizon, knots, pop, msg);
+        if (vs != EMPC_OK) return fail(nullptr, vs, msg);
+    }
     empc_config cfg;
     if (cfg_in) cfg = *cfg_in; else empc_config_default(&cfg);
     if (cfg.elite == 0) cfg.elite = std::max(1, pop / 16);
@@ -539,26 +508,6 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
         return fail(nullptr, EMPC_EINVAL, "need refine_steps >= 0, ckpt_every >= 0, refine_lr >= 0");
     if (cfg.refine_steps > 0 && n > 64)
         return fail(nullptr, EMPC_EUNSUPPORTED, "refinement needs n <= 64");
-    if (!finite_all(A, (size_t)n * n) || !finite_all(B, (size_t)n * m) ||
-        !finite_all(Q, (size_t)n * n) || !finite_all(R, (size_t)m * m) ||
-        !finite_all(bounds, (size_t)m * 2))
-        return fail(nullptr, EMPC_EINVAL, "non-finite model, weight or bound");
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-            if (i != j && Q[(size_t)i * n + j] != 0.0)
-                return fail(nullptr, EMPC_EUNSUPPORTED, "Q must be diagonal");
-    for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j)
-            if (i != j && R[(size_t)i * m + j] != 0.0)
-                return fail(nullptr, EMPC_EUNSUPPORTED, "R must be diagonal");
-    for (int i = 0; i < n; ++i)
-        if (Q[(size_t)i * n + i] < 0.0) return fail(nullptr, EMPC_EINVAL, "Q must be >= 0");
-    for (int i = 0; i < m; ++i) {
-        if (R[(size_t)i * m + i] < 0.0) return fail(nullptr, EMPC_EINVAL, "R must be >= 0");
-        if (!(bounds[2 * i] <= bounds[2 * i + 1]))
-            return fail(nullptr, EMPC_EINVAL, "need u_min <= u_max");
-    }
-
     empc_handle h = new empc_problem_s();
     h->n = n;
     h->m = m;
@@ -591,37 +540,19 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
                                : std::max(1, (int)std::ceil(std::sqrt((double)horizon)));
 
     // host-side staging of the model in FP32
-    std::vector<float> Dm((size_t)n * n), BT((size_t)m * n), qd(n), rd(m), lo(m), hi(m);
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-            Dm[(size_t)i * n + j] = (float)(A[(size_t)i * n + j] - (i == j ? 1.0 : 0.0));
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < m; ++j) BT[(size_t)j * n + i] = (float)B[(size_t)i * m + j];
-    for (int i = 0; i < n; ++i) qd[i] = (float)Q[(size_t)i * n + i];
-    for (int i = 0; i < m; ++i) {
-        rd[i] = (float)R[(size_t)i * m + i];
-        lo[i] = (float)bounds[2 * i];
-        hi[i] = (float)bounds[2 * i + 1];
-    }
-    std::vector<KnotStep> ks;
-    std::vector<double> w0, w1;
-    std::vector<int> idx;
-    make_knot_table(horizon, knots, ks, w0, w1, idx);
-    // Gram of the knot weights: sum_k u_k' R u_k = sum_i r_i U_i' W U_i with
-    // W tridiagonal: W_aa = sum_k w_ka^2, W_a,a+1 = sum_k w_ka w_k,a+1.
-    std::vector<double> Wd(knots, 0.0), Wo(knots, 0.0);
-    for (int k = 0; k < horizon; ++k) {
-        Wd[idx[k]] += w0[k] * w0[k];
-        if (knots > 1) {
-            Wd[idx[k] + 1] += w1[k] * w1[k];
-            Wo[idx[k]] += w0[k] * w1[k];
-        }
-    }
-    std::vector<float> gram(2 * (size_t)knots);
-    for (int a = 0; a < knots; ++a) {
-        gram[a] = (float)Wd[a];
-        gram[knots + a] = (float)Wo[a];
-    }
+    empc::HostTables tb;
+    empc::build_tables(A, B, Q, R, bounds, n, m, horizon, knots, tb);
+    const std::vector<float>& Dm = tb.D;
+    const std::vector<float>& BT = tb.BT;
+    const std::vector<float>& qd = tb.qd;
+    const std::vector<float>& rd = tb.rd;
+    const std::vector<float>& lo = tb.lo;
+    const std::vector<float>& hi = tb.hi;
+    const std::vector<float>& gram = tb.gram;
+    const std::vector<KnotStep>& ks = tb.ks;
+    const std::vector<double>& w0 = tb.w0;
+    const std::vector<double>& w1 = tb.w1;
+    const std::vector<int>& idx = tb.idx;
     if (cfg.refine_steps > 0) {
         if (cfg.refine_lr > 0.0f) {
             h->eta = cfg.refine_lr;
@@ -703,7 +634,7 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal, in
     if (!x0 || !x_goal || !best_knots || !best_cost)
         return fail(h, EMPC_EINVAL, "NULL x0, x_goal or output pointer");
     if (generations < 1) return fail(h, EMPC_EINVAL, "generations must be >= 1");
-    if (!finite_all(x0, h->n) || !finite_all(x_goal, h->n))
+    if (!empc::all_finite(x0, h->n) || !empc::all_finite(x_goal, h->n))
         return fail(h, EMPC_EINVAL, "non-finite x0 or x_goal");
     float* st_in = h->stage;
     for (int i = 0; i < h->n; ++i) {
@@ -905,7 +836,7 @@ empc_status empc_discretize_zoh(const double* Ac, const double* Bc, int n, int m
     if (!Ac || !Bc || !Ad || !Bd) return fail(nullptr, EMPC_EINVAL, "NULL pointer");
     if (n < 1 || m < 0 || !std::isfinite(dt) || dt < 0.0)
         return fail(nullptr, EMPC_EINVAL, "need n >= 1, m >= 0, finite dt >= 0");
-    if (!finite_all(Ac, (size_t)n * n) || !finite_all(Bc, (size_t)n * m))
+    if (!empc::all_finite(Ac, (size_t)n * n) || !empc::all_finite(Bc, (size_t)n * m))
         return fail(nullptr, EMPC_EINVAL, "non-finite Ac or Bc");
     const int N = n + m;
     std::vector<double> M((size_t)N * N, 0.0), E;

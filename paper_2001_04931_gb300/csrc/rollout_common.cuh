@@ -156,11 +156,20 @@ __device__ __forceinline__ void state_product(const float (&d)[R][NX], const flo
         for (int c = 0; c < C; ++c) acc[r][c] += odd[r][c];
 }
 
+// Population loads: through the read-only path when the population cannot
+// change during the kernel, else through L2 (other CTAs of a persistent
+// kernel write it).
+template <bool COHERENT>
+__device__ __forceinline__ float pop_load(const float* p) {
+    if constexpr (COHERENT) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // Breed (cold / warm, Algorithm 1) or load (eval) the knots of candidates
 // c0 .. c0+count-1 into Us[q][t] (leading dimension xs); bred knots also go
 // to pop_out.  Work is spread over `nthr` threads with index `tid`; WARP
 // selects warp- or block-level synchronization.
-template <bool WARP>
+template <bool WARP, bool COHERENT = false>
 __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, int c0,
                            int count, uint32_t gen, int tid, int nthr) {
     const int D = a.m * a.p;
@@ -171,11 +180,12 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
             int s1 = 0, s2 = -1;
             if (c < a.P) {
                 if (c < a.E) {
-                    s1 = a.elite_idx[c];
+                    s1 = COHERENT ? __ldcg(a.elite_idx + c) : a.elite_idx[c];
                 } else {
                     const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawParents, 0u);
-                    s1 = a.elite_idx[parent_rank(o.w[0], a.E)];
-                    s2 = a.elite_idx[parent_rank(o.w[1], a.E)];
+                    const int* ei = a.elite_idx;
+                    s1 = COHERENT ? __ldcg(ei + parent_rank(o.w[0], a.E)) : ei[parent_rank(o.w[0], a.E)];
+                    s2 = COHERENT ? __ldcg(ei + parent_rank(o.w[1], a.E)) : ei[parent_rank(o.w[1], a.E)];
                 }
             }
             par[2 * t] = s1;
@@ -193,7 +203,7 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
             if (a.mode == kEval) {
 #pragma unroll
                 for (int w = 0; w < 4; ++w)
-                    if (q0 + w < D) v[w] = a.pop_in[(size_t)(q0 + w) * a.P + c];
+                    if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + c);
             } else if (a.mode == kCold) {
                 const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawInit, (uint32_t)quad);
 #pragma unroll
@@ -211,7 +221,7 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
                 if (s2 < 0) {
 #pragma unroll
                     for (int w = 0; w < 4; ++w)
-                        if (q0 + w < D) v[w] = __ldg(a.pop_in + (size_t)(q0 + w) * a.P + s1);
+                        if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + s1);
                 } else {
                     const uint32_t cross =
                         draw(a.seed, (uint32_t)c, gen, kDrawCross, (uint32_t)(quad >> 2)).w[quad & 3];
@@ -221,8 +231,8 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
                     for (int w = 0; w < 4; ++w) {
                         const int q = q0 + w;
                         const uint32_t cb = (cross >> (8 * w)) & 0xFFu;
-                        mate[w] = q < D ? __ldg(a.pop_in + (size_t)q * a.P +
-                                                (cb < (uint32_t)a.pc256 ? s2 : s1))
+                        mate[w] = q < D ? pop_load<COHERENT>(a.pop_in + (size_t)q * a.P +
+                                                             (cb < (uint32_t)a.pc256 ? s2 : s1))
                                         : 0.0f;
                     }
                     Words4 gw;

@@ -122,6 +122,7 @@ RolloutArgs base_args(empc_handle h) {
     a.pc256 = h->cfg.p_cross_256;
     a.pm256 = h->cfg.p_mutate_256;
     a.gate = h->cfg.gate;
+    a.status = h->status;
     return a;
 }
 
@@ -311,6 +312,12 @@ empc_status autotune(empc_handle h) {
     a.pop_out = h->pop[0];
     a.cost = h->cost;
     a.gen = nullptr;
+    if (h->cfg.precision == EMPC_BF16) {
+        h->shape = TileShape{2, 128, 1, 1, 1};
+        EMPC_CUDA(h, empc::launch_rollout(a, h->shape, h->stream));
+        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+        return EMPC_OK;
+    }
     if (h->cfg.tile > 0) {
         const size_t k = (size_t)(h->cfg.tile - 1);
         if (k >= ok.size()) return fail(h, EMPC_EINVAL, "cfg.tile out of range");
@@ -502,8 +509,12 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
         cfg.p_mutate_256 > 256)
         return fail(nullptr, EMPC_EINVAL, "probabilities *256 must lie in [0, 256]");
     if (cfg.gate < 0 || cfg.gate > 2) return fail(nullptr, EMPC_EINVAL, "bad gate mode");
-    if (cfg.precision != EMPC_FP32)
-        return fail(nullptr, EMPC_EUNSUPPORTED, "only FP32 precision is built");
+    if (cfg.precision != EMPC_FP32 && cfg.precision != EMPC_BF16)
+        return fail(nullptr, EMPC_EINVAL, "unknown precision");
+    if (cfg.precision == EMPC_BF16 && !empc::rollout_bf16_supported(n, m, horizon))
+        return fail(nullptr, EMPC_EUNSUPPORTED, "BF16 tensor-core rollout needs n <= 128, m <= 64");
+    if (cfg.precision == EMPC_BF16 && cfg.refine_steps > 0)
+        return fail(nullptr, EMPC_EUNSUPPORTED, "refinement runs in FP32 only");
     if (cfg.refine_steps < 0 || cfg.ckpt_every < 0 || !(cfg.refine_lr >= 0.0f))
         return fail(nullptr, EMPC_EINVAL, "need refine_steps >= 0, ckpt_every >= 0, refine_lr >= 0");
     if (cfg.refine_steps > 0 && n > 64)
@@ -655,6 +666,7 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal, in
     *best_cost = st_out[h->D];
     int status_bits;
     std::memcpy(&status_bits, st_out + h->D + 1, sizeof(int));
+    if (status_bits & 2) return fail(h, EMPC_ETIMEOUT, "a bounded device wait gave up");
     if (status_bits & 1) return fail(h, EMPC_ENONFINITE, "best cost is not finite");
     return EMPC_OK;
 }

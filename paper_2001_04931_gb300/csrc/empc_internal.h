@@ -45,6 +45,7 @@ struct RolloutArgs {
     int pc256, pm256, gate;
     int cand_begin;  // first candidate this launch covers (later ones up to P)
     int pdl;         // launch with programmatic stream serialization
+    int* status;     // bit 1 (value 2): a bounded device wait gave up (may be null)
 };
 
 // Launch `kern` with an optional programmatic-stream-serialization attribute
@@ -95,12 +96,17 @@ struct GradArgs {
 cudaError_t launch_grad(const GradArgs& a, int nx, int cands, int wpc, cudaStream_t st);
 size_t grad_smem_bytes(int nx, int nrg, int cands, int wpc, int n, int m, int p, int T, int ce);
 
+// BF16 tensor-core rollout (rollout_bf16.cu): n <= 128, m <= 64.
+cudaError_t launch_rollout_bf16(const RolloutArgs& a, cudaStream_t st);
+bool rollout_bf16_supported(int n, int m, int T);
+size_t rollout_bf16_smem_bytes(int T);
+
 // Rollout tile.  kind 0 (block): ceil(n/rows) threads per candidate group,
 // `groups` candidate groups per CTA, one block barrier per step.  kind 1
 // (warp): each warp owns whole candidates (32/nrg groups of `cands`), `groups`
 // warps per CTA, one warp barrier per step.
 struct TileShape {
-    int kind;   // 0 block, 1 warp
+    int kind;   // 0 block, 1 warp, 2 BF16 tensor-core tile of 128 candidates
     int nx;     // compiled state dimension (>= n)
     int rows;   // state rows per thread
     int cands;  // candidates per thread (1, 2 or 4)

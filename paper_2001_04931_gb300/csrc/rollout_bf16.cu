@@ -1,0 +1,394 @@
+// Fused breed + rollout + cost with the per-step product on the tensor cores
+// (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+//
+// For a tile of 128 candidates the step x_{k+1} = x_k + D x_k + B_d u_k
+// (D = A_d - I, Eq. first_order_integration in delta form) is one
+// 128 x 128 x 192 contraction per step:
+//   Y[c][i] = sum_{k<128} x_c[k] D[i][k] + sum_{j<64} u_c[j] B_d[i][j],
+// with A = [x_c | u_c] (candidates x K, BF16) and B = [D | B_d] (states x K,
+// BF16, constant), both K-major with the 128-byte swizzle in shared memory,
+// and Y in tensor memory (TMEM lane = candidate, column = state).  Two
+// threads own each candidate (its TMEM lane), one per half of the states,
+// whose FP32 master copy they keep in registers: each adds Y to its states,
+// accumulates their stage cost (x_{k+1}-g)' Q (x_{k+1}-g) in eight partial
+// sums, rounds the new states and half of the next input u_{k+1} (knots kept
+// in registers per segment) to BF16, and writes them into the next step's A
+// row.  A is double-buffered: the next input is written while the step's
+// MMAs run, and each step's product runs as two N = 64 halves, one per
+// thread group, so one group's epilogue overlaps the other half's MMAs.  The input cost sum_k u_k' R u_k is added in closed form from
+// the knots (Gram of the knot weights), in FP32.
+//
+// Precision: D, B_d, x and u enter the product as BF16 (relative rounding
+// 2^-9); accumulation, the state update and the cost stay FP32.  Every
+// mbarrier wait is bounded: past the limit the kernel sets status bit 2,
+// leaves the step loop, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "rollout_common.cuh"
+
+namespace empc {
+namespace {
+
+constexpr int kTileCands = 128;  // M: candidates per CTA (TMEM lanes)
+constexpr int kKx = 128;         // K columns for the state (n padded)
+constexpr int kKu = 64;          // K columns for the input (m padded)
+constexpr int kK = kKx + kKu;    // 192
+constexpr int kAtomBytes = 128 * 128;  // one 64-column swizzle atom of 128 rows
+constexpr int kOperandBytes = 3 * kAtomBytes;  // 128 rows x 192 BF16
+constexpr uint32_t kTmemCols = 128;    // the accumulator
+constexpr long long kWaitPolls = 1ll << 26;
+constexpr int kThreads = 2 * kTileCands;  // two thread groups of 128 (4 warps each)
+constexpr int kKuHalf = kKu / 2;          // inputs per thread
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (row r, column k) in a K-major 128-row operand with
+// the 128-byte swizzle: 64-column atoms of 128 rows x 128 B, 16-byte chunks
+// xor-ed with the row within its group of 8.
+__host__ __device__ __forceinline__ uint32_t swz(int r, int k) {
+    return (uint32_t)((k >> 6) * kAtomBytes + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4) +
+                      ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long it = 0; it < kWaitPolls; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(addr));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Paired FP32 add and multiply (add/mul.rn.f32x2, sm_100 and later).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Store 8 consecutive K values (BF16) of row r starting at column k (k % 8 == 0).
+__device__ __forceinline__ void put8(uint8_t* op, int r, int k, const float* v) {
+    uint4 q;
+    q.x = pack_bf16(v[0], v[1]);
+    q.y = pack_bf16(v[2], v[3]);
+    q.z = pack_bf16(v[4], v[5]);
+    q.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(op + swz(r, k)) = q;
+}
+
+struct Bf16Layout {
+    static constexpr int kA0 = 0;                      // A buffer 0
+    static constexpr int kA1 = kOperandBytes;          // A buffer 1
+    static constexpr int kB = 2 * kOperandBytes;       // B = [D | B_d]
+    static constexpr int kG = 3 * kOperandBytes;       // goal [128] f32
+    static constexpr int kQ = kG + 128 * 4;            // diag Q [128] f32
+    static constexpr int kKnots = kQ + 128 * 4;        // KnotStep[T]
+    __host__ __device__ static int par(int T) { return kKnots + 16 * T; }  // int[2*128]
+    __host__ __device__ static int part(int T) { return par(T) + 8 * kTileCands; }  // f32[128]
+    __host__ __device__ static int total(int T) { return part(T) + 4 * kTileCands + 1024; }
+};
+
+__global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const RolloutArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t* sA[2] = {sm + Bf16Layout::kA0, sm + Bf16Layout::kA1};
+    uint8_t* sB = sm + Bf16Layout::kB;
+    float* sg = reinterpret_cast<float*>(sm + Bf16Layout::kG);
+    float* sq = reinterpret_cast<float*>(sm + Bf16Layout::kQ);
+    KnotStep* ks = reinterpret_cast<KnotStep*>(sm + Bf16Layout::kKnots);
+    int* par = reinterpret_cast<int*>(sm + Bf16Layout::par(a.T));
+    float* spart = reinterpret_cast<float*>(sm + Bf16Layout::part(a.T));
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int grp = warp >> 2;                     // state half / input half of this thread
+    const int row = ((warp & 3) << 5) | (tid & 31);  // candidate row = TMEM lane
+    const int n = a.n, m = a.m, p = a.p, T = a.T;
+    const int c0 = a.cand_begin + blockIdx.x * kTileCands;
+    const int cand = c0 + row;
+    pdl_launch_dependents();
+
+    // ---- constant operand B = [D | B_d] (rows = states), goal, Q, knot table
+    for (int idx = tid; idx < 128 * (kK / 8); idx += blockDim.x) {  // (all threads)
+        const int i = idx / (kK / 8), k0 = (idx % (kK / 8)) * 8;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + e;
+            float x = 0.0f;
+            if (i < n) {
+                if (k < kKx) x = k < n ? a.D[i * n + k] : 0.0f;
+                else if (k - kKx < m) x = a.BT[(k - kKx) * n + i];
+            }
+            v[e] = x;
+        }
+        put8(sB, i, k0, v);
+    }
+    for (int i = tid; i < 128; i += blockDim.x) {
+        sg[i] = i < n ? a.goal[i] : 0.0f;
+        sq[i] = i < n ? a.qdiag[i] : 0.0f;
+    }
+    for (int k = tid; k < T; k += blockDim.x) ks[k] = a.ktab[k];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        abort_sh = 0;
+    }
+
+    // ---- knots: bred (to pop_out) or given (pop_in)
+    pdl_wait_primary();
+    const uint32_t gen = a.gen ? *a.gen : 0u;
+    if (a.mode == kWarm && grp == 0) {
+        int s1, s2;
+        parents_of<false>(a, cand, gen, s1, s2);
+        par[2 * row] = s1;
+        par[2 * row + 1] = s2;
+    }
+    __syncthreads();
+    const int D = m * p;
+    if (a.mode != kEval) {
+        const int nquad = (D + 3) >> 2;
+        for (int it = tid; it < nquad * kTileCands; it += blockDim.x) {
+            const int t = it % kTileCands, quad = it / kTileCands;
+            const int c = c0 + t;
+            if (c >= a.P) continue;
+            float v[4];
+            breed_quad<false>(a, c, quad, gen, a.mode == kWarm ? par[2 * t] : 0,
+                              a.mode == kWarm ? par[2 * t + 1] : -1, v);
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if (quad * 4 + w < D) a.pop_out[(size_t)(quad * 4 + w) * a.P + c] = v[w];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // bred knots visible to the block; TMEM base published
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const float* src = a.mode == kEval ? a.pop_in : a.pop_out;
+    const bool live = cand < a.P;
+
+    // ---- initial state: FP32 master of own half in registers, BF16 copy in A[0]
+    float xs[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        const int i = grp * 64 + j;
+        xs[j] = i < n ? a.x0[i] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 64; j += 8) put8(sA[0], row, grp * 64 + j, xs + j);
+    // knots of the current segment (own half of the inputs)
+    float ua[kKuHalf], ub[kKuHalf];
+    const int i0 = grp * kKuHalf;
+    int seg = -1;
+    float Ju = 0.0f;  // input cost of own inputs, closed form, accumulated per segment
+    auto load_segment = [&](int s) {
+#pragma unroll
+        for (int j = 0; j < kKuHalf; ++j) {
+            const int i = i0 + j;
+            ua[j] = (live && i < m) ? src[(size_t)(i * p + s) * a.P + cand] : 0.0f;
+            ub[j] = (live && i < m && s + 1 < p) ? src[(size_t)(i * p + s + 1) * a.P + cand] : 0.0f;
+        }
+        // segments come in order, each once: W_ss U_s^2 + 2 W_s,s+1 U_s U_s+1,
+        // plus W_{p-1,p-1} U_{p-1}^2 with the last segment
+        const float wd = a.gram[s];
+        const float wo = s + 1 < p ? 2.0f * a.gram[p + s] : 0.0f;
+        const float wl = s + 2 == p ? a.gram[s + 1] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < kKuHalf; ++j) {
+            if (i0 + j < m) {
+                float t = wd * ua[j] * ua[j];
+                t = fmaf(wo * ua[j], ub[j], t);
+                t = fmaf(wl * ub[j], ub[j], t);
+                Ju = fmaf(a.rdiag[i0 + j], t, Ju);
+            }
+        }
+    };
+    auto write_input = [&](uint8_t* op, const KnotStep& st) {
+        if (st.idx1 != seg) {
+            seg = st.idx1;
+            load_segment(seg);
+        }
+#pragma unroll
+        for (int j = 0; j < kKuHalf; j += 8) {
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = fmaf(st.w1, ub[j + e], st.w0 * ua[j + e]);
+            put8(op, row, kKx + i0 + j, v);
+        }
+    };
+    write_input(sA[0], ks[0]);
+
+    float2 jacc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                      make_float2(0.f, 0.f)};
+    bool ok = true;
+    const uint32_t idesc = idesc_bf16(64);
+    for (int k = 0; k < T; ++k) {
+        uint8_t* Acur = sA[k & 1];
+        uint8_t* Anext = sA[(k + 1) & 1];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (!__syncthreads_and(ok)) break;  // every thread leaves together
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(Acur), b0 = smem_u32(sB);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int kk = 0; kk < kK / 16; ++kk) {
+                    const uint32_t off = (kk >> 2) * kAtomBytes + (kk & 3) * 32;
+                    mma_bf16(tmem + h * 64, sdesc(a0 + off), sdesc(b0 + off + h * 64 * 128), idesc,
+                             kk > 0 ? 1u : 0u);
+                }
+                mma_commit(&mbar[h]);
+            }
+        }
+        // off the critical path: the next input, while the MMAs run (Anext was
+        // last read by the previous step's MMAs, which have completed)
+        if (k + 1 < T) write_input(Anext, ks[k + 1]);
+        // epilogue of this thread's half of the states
+        if (!mbar_wait(&mbar[grp], (uint32_t)(k & 1))) {
+            ok = false;
+            continue;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const int ch = 2 * grp + c2;
+            float y[32];
+            tmem_ld32(lane_base + ch * 32, y);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const float4* g4 = reinterpret_cast<const float4*>(sg + ch * 32);
+            const float4* q4 = reinterpret_cast<const float4*>(sq + ch * 32);
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                const int jj = c2 * 32 + j;
+                const float4 gg = g4[j / 4], qq = q4[j / 4];
+                const float2 x01 = add2(make_float2(xs[jj], xs[jj + 1]), make_float2(y[j], y[j + 1]));
+                const float2 x23 = add2(make_float2(xs[jj + 2], xs[jj + 3]), make_float2(y[j + 2], y[j + 3]));
+                xs[jj] = x01.x; xs[jj + 1] = x01.y; xs[jj + 2] = x23.x; xs[jj + 3] = x23.y;
+                const float2 e01 = add2(x01, make_float2(-gg.x, -gg.y));
+                const float2 e23 = add2(x23, make_float2(-gg.z, -gg.w));
+                jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[(j / 4) & 3]);
+                jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[(j / 4) & 3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) put8(Anext, row, ch * 32 + j, xs + c2 * 32 + j);
+        }
+    }
+    if (!ok) abort_sh = 1;
+    float jown = Ju;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) jown += jacc[j].x + jacc[j].y;
+    if (grp == 1) spart[row] = jown;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (abort_sh) {
+        if (tid == 0 && a.status) atomicOr(a.status, 2);
+    } else if (live && grp == 0) {
+        a.cost[cand] = finite_or_inf(jown + spart[row]);
+    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+}
+
+}  // namespace
+
+size_t rollout_bf16_smem_bytes(int T) { return (size_t)Bf16Layout::total(T); }
+
+bool rollout_bf16_supported(int n, int m, int T) {
+    return n <= kKx && m <= kKu && rollout_bf16_smem_bytes(T) <= 227u * 1024u;
+}
+
+cudaError_t launch_rollout_bf16(const RolloutArgs& a, cudaStream_t st) {
+    if (!rollout_bf16_supported(a.n, a.m, a.T)) return cudaErrorInvalidConfiguration;
+    const size_t smem = rollout_bf16_smem_bytes(a.T);
+    static int smem_cap = 48 * 1024;
+    if ((int)smem > smem_cap) {
+        cudaError_t e = cudaFuncSetAttribute(rollout_bf16_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_cap = (int)smem;
+    }
+    const int grid = (a.P - a.cand_begin + kTileCands - 1) / kTileCands;
+    if (grid <= 0) return cudaSuccess;
+    return launch_kernel(rollout_bf16_kernel, dim3(grid), dim3(kThreads), smem, st,
+                         a.pdl != 0, a);
+}
+
+}  // namespace empc

@@ -172,17 +172,20 @@ int rollout_shapes(int n, TileShape* out, int cap) {
 }
 
 int rollout_threads(const TileShape& s, int n) {
+    if (s.kind == 2) return 128;
     if (s.kind == 1) return 32 * s.groups;
     return ((n + s.rows - 1) / s.rows) * s.groups;
 }
 
 int rollout_cands_per_cta(const TileShape& s, int n) {
+    if (s.kind == 2) return 128;
     if (s.kind == 1) return s.groups * (32 / warp_nrg(s.nx)) * s.cands;
     (void)n;
     return s.groups * s.cands;
 }
 
 size_t rollout_smem_bytes(const TileShape& s, int n, int m, int p, int T) {
+    if (s.kind == 2) return rollout_bf16_smem_bytes(T);
     if (s.kind == 1) {
         const int nrg = warp_nrg(s.nx);
         const int xr = nrg * s.rows;
@@ -207,6 +210,7 @@ bool rollout_shape_supported(const TileShape& s, int n, int m, int p, int T) {
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, const TileShape& s, cudaStream_t st) {
+    if (s.kind == 2) return launch_rollout_bf16(a, st);
     if (s.nx != compiled_nx(a.n)) return cudaErrorInvalidConfiguration;
     return s.kind == 1 ? launch_rollout_warp(a, s, st) : launch_rollout_block(a, s, st);
 }

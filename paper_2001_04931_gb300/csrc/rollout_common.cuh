@@ -165,10 +165,103 @@ __device__ __forceinline__ float pop_load(const float* p) {
     else return __ldg(p);
 }
 
+// Parents of child c as population columns (s1, s2); s2 < 0 marks an elite
+// slot (c < E) copied unchanged from column s1.  Warm start only.
+template <bool COHERENT>
+__device__ __forceinline__ void parents_of(const RolloutArgs& a, int c, uint32_t gen, int& s1,
+                                           int& s2) {
+    s1 = 0;
+    s2 = -1;
+    if (c >= a.P) return;
+    if (c < a.E) {
+        s1 = COHERENT ? __ldcg(a.elite_idx + c) : a.elite_idx[c];
+    } else {
+        const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawParents, 0u);
+        const int* ei = a.elite_idx;
+        s1 = COHERENT ? __ldcg(ei + parent_rank(o.w[0], a.E)) : ei[parent_rank(o.w[0], a.E)];
+        s2 = COHERENT ? __ldcg(ei + parent_rank(o.w[1], a.E)) : ei[parent_rank(o.w[1], a.E)];
+    }
+}
+
+// Knots q0 .. q0+3 (q0 = 4 quad) of candidate c < P: loaded (eval), drawn
+// (cold), or mated and mutated from parent columns s1, s2 (warm), as
+// Algorithm 1's cold / warm branches specify.
+template <bool COHERENT>
+__device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad, uint32_t gen,
+                                           int s1, int s2, float (&v)[4]) {
+    const int D = a.m * a.p;
+    const int q0 = quad * 4;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) v[w] = 0.0f;
+    if (a.mode == kEval) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + c);
+    } else if (a.mode == kCold) {
+        const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawInit, (uint32_t)quad);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int q = q0 + w;
+            if (q < D) {
+                const int i = q / a.p;
+                const float lo = a.umin[i], hi = a.umax[i];
+                v[w] = clamp_to(__fmaf_rn(__fsub_rn(hi, lo), unit_closed_open(o.w[w]), lo), lo, hi);
+            }
+        }
+    } else if (s2 < 0) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + s1);
+    } else {
+        const uint32_t cross =
+            draw(a.seed, (uint32_t)c, gen, kDrawCross, (uint32_t)(quad >> 2)).w[quad & 3];
+        // issue the parent-knot gathers before the remaining draws
+        float mate[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int q = q0 + w;
+            const uint32_t cb = (cross >> (8 * w)) & 0xFFu;
+            mate[w] = q < D ? pop_load<COHERENT>(a.pop_in + (size_t)q * a.P +
+                                                 (cb < (uint32_t)a.pc256 ? s2 : s1))
+                            : 0.0f;
+        }
+        Words4 gw;
+        uint32_t gate_blk = 0xFFFFFFFFu;
+        float z[4];
+        bool have_z = false;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int q = q0 + w;
+            if (q >= D) continue;
+            const int i = q / a.p;
+            bool mut = true;
+            if (a.gate != 2) {
+                const uint32_t gb = (a.gate == 0) ? (uint32_t)i : (uint32_t)q;
+                if ((gb >> 4) != gate_blk) {
+                    gate_blk = gb >> 4;
+                    gw = draw(a.seed, (uint32_t)c, gen, kDrawGate, gate_blk);
+                }
+                mut = ((gw.w[(gb >> 2) & 3u] >> (8u * (gb & 3u))) & 0xFFu) < (uint32_t)a.pm256;
+            }
+            float val = mate[w];
+            if (mut) {
+                if (!have_z) {
+                    const Words4 nz = draw(a.seed, (uint32_t)c, gen, kDrawNoise, (uint32_t)quad);
+                    gauss_pair(nz.w[0], nz.w[1], &z[0], &z[1]);
+                    gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
+                    have_z = true;
+                }
+                val = __fmaf_rn(a.sigma, z[w], mate[w]);
+            }
+            v[w] = clamp_to(val, a.umin[i], a.umax[i]);
+        }
+    }
+}
+
 // Breed (cold / warm, Algorithm 1) or load (eval) the knots of candidates
-// c0 .. c0+count-1 into Us[q][t] (leading dimension xs); bred knots also go
-// to pop_out.  Work is spread over `nthr` threads with index `tid`; WARP
-// selects warp- or block-level synchronization.
+// c0 .. c0+count-1 into Us[q][t] (leading dimension xs; skipped when Us is
+// null); bred knots also go to pop_out.  Work is spread over `nthr` threads
+// with index `tid`; WARP selects warp- or block-level synchronization.
 template <bool WARP, bool COHERENT = false>
 __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, int c0,
                            int count, uint32_t gen, int tid, int nthr) {
@@ -176,18 +269,8 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
     const int nquad = (D + 3) >> 2;
     if (a.mode == kWarm) {
         for (int t = tid; t < count; t += nthr) {
-            const int c = c0 + t;
-            int s1 = 0, s2 = -1;
-            if (c < a.P) {
-                if (c < a.E) {
-                    s1 = COHERENT ? __ldcg(a.elite_idx + c) : a.elite_idx[c];
-                } else {
-                    const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawParents, 0u);
-                    const int* ei = a.elite_idx;
-                    s1 = COHERENT ? __ldcg(ei + parent_rank(o.w[0], a.E)) : ei[parent_rank(o.w[0], a.E)];
-                    s2 = COHERENT ? __ldcg(ei + parent_rank(o.w[1], a.E)) : ei[parent_rank(o.w[1], a.E)];
-                }
-            }
+            int s1, s2;
+            parents_of<COHERENT>(a, c0 + t, gen, s1, s2);
             par[2 * t] = s1;
             par[2 * t + 1] = s2;
         }
@@ -197,84 +280,15 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
         const int t = it % count;
         const int quad = it / count;
         const int c = c0 + t;
-        const int q0 = quad * 4;
         float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (c < a.P) {
-            if (a.mode == kEval) {
-#pragma unroll
-                for (int w = 0; w < 4; ++w)
-                    if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + c);
-            } else if (a.mode == kCold) {
-                const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawInit, (uint32_t)quad);
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const int q = q0 + w;
-                    if (q < D) {
-                        const int i = q / a.p;
-                        const float lo = a.umin[i], hi = a.umax[i];
-                        v[w] = clamp_to(__fmaf_rn(__fsub_rn(hi, lo), unit_closed_open(o.w[w]), lo),
-                                        lo, hi);
-                    }
-                }
-            } else {
-                const int s1 = par[2 * t], s2 = par[2 * t + 1];
-                if (s2 < 0) {
-#pragma unroll
-                    for (int w = 0; w < 4; ++w)
-                        if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + s1);
-                } else {
-                    const uint32_t cross =
-                        draw(a.seed, (uint32_t)c, gen, kDrawCross, (uint32_t)(quad >> 2)).w[quad & 3];
-                    // issue the parent-knot gathers before the remaining draws
-                    float mate[4];
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const int q = q0 + w;
-                        const uint32_t cb = (cross >> (8 * w)) & 0xFFu;
-                        mate[w] = q < D ? pop_load<COHERENT>(a.pop_in + (size_t)q * a.P +
-                                                             (cb < (uint32_t)a.pc256 ? s2 : s1))
-                                        : 0.0f;
-                    }
-                    Words4 gw;
-                    uint32_t gate_blk = 0xFFFFFFFFu;
-                    float z[4];
-                    bool have_z = false;
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const int q = q0 + w;
-                        if (q >= D) continue;
-                        const int i = q / a.p;
-                        bool mut = true;
-                        if (a.gate != 2) {
-                            const uint32_t gb = (a.gate == 0) ? (uint32_t)i : (uint32_t)q;
-                            if ((gb >> 4) != gate_blk) {
-                                gate_blk = gb >> 4;
-                                gw = draw(a.seed, (uint32_t)c, gen, kDrawGate, gate_blk);
-                            }
-                            mut = ((gw.w[(gb >> 2) & 3u] >> (8u * (gb & 3u))) & 0xFFu) <
-                                  (uint32_t)a.pm256;
-                        }
-                        float val = mate[w];
-                        if (mut) {
-                            if (!have_z) {
-                                const Words4 nz =
-                                    draw(a.seed, (uint32_t)c, gen, kDrawNoise, (uint32_t)quad);
-                                gauss_pair(nz.w[0], nz.w[1], &z[0], &z[1]);
-                                gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
-                                have_z = true;
-                            }
-                            val = __fmaf_rn(a.sigma, z[w], mate[w]);
-                        }
-                        v[w] = clamp_to(val, a.umin[i], a.umax[i]);
-                    }
-                }
-            }
-        }
+        if (c < a.P)
+            breed_quad<COHERENT>(a, c, quad, gen, a.mode == kWarm ? par[2 * t] : 0,
+                                 a.mode == kWarm ? par[2 * t + 1] : -1, v);
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const int q = q0 + w;
+            const int q = quad * 4 + w;
             if (q < D) {
-                Us[q * xs + t] = v[w];
+                if (Us) Us[q * xs + t] = v[w];
                 if (a.mode != kEval && c < a.P) a.pop_out[(size_t)q * a.P + c] = v[w];
             }
         }

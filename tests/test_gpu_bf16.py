@@ -1,0 +1,75 @@
+"""BF16 tensor-core rollout (tcgen05) against the FP64 oracle.
+
+Breeding is the same FP32 code as the CUDA-core path, so bred populations
+match the oracle bit for bit.  The per-step product takes D, B_d, x and u in
+BF16 (unit roundoff 2^-9 = 2e-3) with FP32 accumulation, so the cost is only
+close: these tests bound the relative cost error at 3e-2 (max) and 5e-3
+(median) on the workloads below, and require the elite set to be drawn from
+the FP64 cost order within that tolerance."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from helpers import gpu_problem, oracle_model, rel_err
+
+pytestmark = pytest.mark.gpu
+MAX_RTOL, MED_RTOL = 3e-2, 5e-3
+
+
+def _eval(prob, x0, g, pop_np):
+    import torch
+    pop = torch.from_numpy(np.ascontiguousarray(pop_np, np.float32)).cuda()
+    cost = torch.empty(pop.shape[1], device="cuda")
+    prob.evaluate(torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                  torch.tensor(g, dtype=torch.float32, device="cuda"), pop, cost)
+    torch.cuda.synchronize()
+    return cost.cpu().numpy()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(dof=64, radius=3, dt=0.005, T=60, p=8, P=300, E=16, q_pos=10.0, q_vel=1.0, r=1e-4),
+    dict(dof=4, T=30, p=4, P=200, E=8),
+    dict(dof=40, radius=3, dt=0.005, T=25, p=3, P=129, E=8),
+])
+def test_bf16_costs_against_oracle(kw):
+    import paper_2001_04931_gb300 as E
+    wl = W.small(**kw)
+    prob = gpu_problem(wl, precision=E.EMPC_BF16)
+    assert prob.info().tile_kind == 2
+    M = oracle_model(wl)
+    x0, g = wl.start_goal()
+    pop = np.random.default_rng(0).uniform(-1, 1, (wl.m * wl.p, wl.P)).astype(np.float32)
+    err = rel_err(_eval(prob, x0, g, pop), M.cost_population(x0, g, pop))
+    assert err.max() <= MAX_RTOL and np.median(err) <= MED_RTOL, (err.max(), np.median(err))
+    prob.close()
+
+
+def test_bf16_lockstep_breeding_bit_exact():
+    import torch
+    import paper_2001_04931_gb300 as E
+    wl = W.small(dof=16, radius=3, dt=0.005, T=40, p=5, P=256, E=16)
+    prob = gpu_problem(wl, seed=7, precision=E.EMPC_BF16)
+    M = oracle_model(wl)
+    x0, g = wl.start_goal()
+    b = wl.bounds().astype(np.float32)
+    prev = None
+    for gen in range(3):
+        prob.solve(x0, g, 1)
+        pop = torch.empty((prob.D, prob.P), device="cuda")
+        cost = torch.empty(prob.P, device="cuda")
+        el = torch.empty(prob.E, device="cuda", dtype=torch.int32)
+        prob.get_state(pop, cost, el)
+        torch.cuda.synchronize()
+        pop, cost, el = pop.cpu().numpy(), cost.cpu().numpy(), el.cpu().numpy()
+        ref = (O.breed_cold(7, gen, b[:, 0], b[:, 1], wl.m, wl.p, wl.P) if prev is None else
+               O.breed_warm(7, gen, prev[0], prev[2], b[:, 0], b[:, 1], wl.m, wl.p, wl.sigma))
+        np.testing.assert_array_equal(pop.view(np.uint32), ref.view(np.uint32))
+        oc = M.cost_population(x0, g, pop)
+        assert rel_err(cost, oc).max() <= MAX_RTOL
+        # elites by the GPU's BF16 costs: every FP64 cost of an elite is within
+        # the tolerance band of the E-th smallest FP64 cost
+        tE = np.sort(oc)[wl.E - 1]
+        assert (oc[el] <= tE * (1 + 2 * MAX_RTOL)).all()
+        prev = (pop, cost, el)
+    prob.close()

@@ -4,9 +4,17 @@
 A step is one EMPC solve: G generations of breed + knot expansion + rollout +
 cost + elite selection over the whole population, starting cold (the same
 work every step).  Default workload: the 24-DoF coupled chain (n=48, m=24,
-T=100, 5 knots, P=4096, E=128, G=30), FP32.
+T=100, 5 knots, P=4096, E=128, G=30), FP32.  Other workloads:
+  c1  2-DoF chain, P=512, T=50, G=20 (FP32)
+  c3  c2 with 5 projected-gradient refinement steps on the elites per
+      generation (adjoint with checkpoints every 10 steps), reported against
+      plain FP32 EMPC at equal final cost
+  c4  256 independent problems (DoF 2-32, T 20-200, P 256-4096) in one
+      persistent launch, reported against solving them one after another
+  c5  64-DoF chain, P=16384, T=200, G=40 on the BF16 tensor cores, reported
+      against the FP32 path
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload c1|c2|c5]
+  python bench.py [--gpus N --steps K --warmup W] [--workload c1|c2|c3|c4|c5]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
 
 Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas, one
@@ -53,8 +61,9 @@ def workload_desc(wl):
 
 def alg_flops_per_candidate(wl):
     """Algorithmic FLOPs of one candidate's rollout and cost in one generation:
-    per step 2n^2 (D x) + 6n (knot lerp 3n, increment n, stage cost 2n... see
-    the design doc), plus 2pnm for the knot forces B U_j and 3mp for the input cost."""
+    per step 2n^2 for D x, 3n for the knot-force blend w0 BU_a + w1 BU_b, n for
+    the state increment and 2n for the weighted state error; plus 2pnm for the
+    knot forces B U_j and 3mp for the tridiagonal input cost."""
     n, m, T, p = wl.n, wl.m, wl.T, wl.p
     return T * (2 * n * n + 6 * n) + 2 * p * n * m + 3 * m * p
 
@@ -121,25 +130,63 @@ def traffic_record(kernel_file):
 
 
 def cpu_baseline(wl, seconds):
-    """The oracle (FP64, as it stands) running Algorithm 1 on the full
-    population on the host cores until `seconds` pass or G generations end."""
+    """The oracle (FP64, as it stands) on the host cores: Algorithm 1 on the
+    full population until `seconds` pass or G generations end; for
+    populations too large for that, the rollout and cost of a sample of
+    candidates."""
     import oracle as O
     A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
     b = wl.bounds()
     M = O.Model(A, B, wl.Q(), wl.R(), b[:, 0], b[:, 1], wl.T, wl.p)
-    ga = O.EMPC(M, wl.P, wl.E, seed=1, sigma=wl.sigma)
     x0, g = wl.start_goal()
+    if wl.P * wl.T * wl.n * wl.n > 4e9:  # one generation would take minutes
+        pop = O.breed_cold(1, 0, b[:, 0].astype(np.float32), b[:, 1].astype(np.float32), wl.m,
+                           wl.p, 4096)
+        S, done, t0 = 64, 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds and done + S <= 4096:
+            M.cost_population(x0, g, pop[:, done:done + S])
+            done += S
+        el = time.perf_counter() - t0
+        return {"value": done * wl.T / el, "unit": UNIT, "cores": O.num_threads(),
+                "kind": "oracle", "seconds": el,
+                "sample": f"rollout + cost of {done} cold-start candidates ({workload_desc(wl)}),"
+                          " FP64 C oracle, OpenMP over candidates"}
+    refine = {}
+    if wl.refine_steps:
+        refine = dict(refine_steps=wl.refine_steps, refine_eta=M.lipschitz_step())
+    ga = O.EMPC(M, wl.P, wl.E, seed=1, sigma=wl.sigma, **refine)
     t0 = time.perf_counter()
     gens = 0
     while gens < wl.G and (gens == 0 or time.perf_counter() - t0 < seconds):
         ga.generation(x0, g)
         gens += 1
     el = time.perf_counter() - t0
+    what = (f"{gens} of {wl.G} generations" + (" (with elite refinement)" if refine else ""))
     return {"value": wl.P * wl.T * gens / el, "unit": UNIT, "cores": O.num_threads(),
             "kind": "oracle",
-            "sample": f"{gens} of {wl.G} generations of the full {wl.P}-candidate population "
+            "sample": f"{what} of the full {wl.P}-candidate population "
                       f"({workload_desc(wl)}), FP64 C oracle, OpenMP over candidates",
             "seconds": el}
+
+
+def cpu_baseline_batch(wls, seconds):
+    """The oracle on the host cores over the batched problems, one generation
+    of Algorithm 1 per problem, until `seconds` pass."""
+    import oracle as O
+    done_units, t0, k = 0, time.perf_counter(), 0
+    while k < len(wls) and (k == 0 or time.perf_counter() - t0 < seconds):
+        wl = wls[k]
+        A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+        b = wl.bounds()
+        M = O.Model(A, B, wl.Q(), wl.R(), b[:, 0], b[:, 1], wl.T, wl.p)
+        x0, g = wl.start_goal()
+        O.EMPC(M, wl.P, wl.E, seed=wl.seed, sigma=wl.sigma).generation(x0, g)
+        done_units += wl.P * wl.T
+        k += 1
+    el = time.perf_counter() - t0
+    return {"value": done_units / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "seconds": el, "sample": f"one generation of each of the first {k} of {len(wls)} "
+                                     "batched problems, FP64 C oracle, OpenMP over candidates"}
 
 
 def run_reference(args, wl):
@@ -180,35 +227,64 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args, wl, rank, world, local_rank):
+def run_reference_batch(args):
+    """The oracle as the reference arm of the batched workload: each step is
+    one generation of Algorithm 1 for a problem of the batch, cycling."""
+    import oracle as O
+    wls = W.batched_problems(256, seed=0)
+    t_budget = 120.0 / max(1, args.steps + args.warmup)
+    models = {}
+
+    def step(k):
+        wl = wls[k % len(wls)]
+        if k % len(wls) not in models:
+            A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+            b = wl.bounds()
+            M = O.Model(A, B, wl.Q(), wl.R(), b[:, 0], b[:, 1], wl.T, wl.p)
+            models[k % len(wls)] = (M, O.EMPC(M, wl.P, wl.E, seed=wl.seed, sigma=wl.sigma))
+        M, ga = models[k % len(wls)]
+        x0, g = wl.start_goal()
+        ga.generation(x0, g)
+        return wl.P * wl.T
+
+    for k in range(args.warmup):
+        step(k)
+    t0, units = time.perf_counter(), 0
+    for k in range(args.steps):
+        units += step(args.warmup + k)
+        if time.perf_counter() - t0 > t_budget * args.steps:
+            break
+    el = time.perf_counter() - t0
+    value = units / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c4: 256 problems (one generation of one problem per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
+                             "kind": "oracle",
+                             "sample": "one generation of successive batched problems per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def measured_bf16_peak():
+    try:
+        rec = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(rec["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 (no measured peak file)"
+
+
+def timed_steps(step_fn, stream, args, local_rank, dist, flush):
+    """W warm-up steps, then K steps each bracketed by CUDA events on
+    `stream`, with the L2 flushed before every step; returns (ms/step,
+    clocks)."""
     import torch
-    import paper_2001_04931_gb300 as E
-
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    wl = W.config(wl.name, seed=rank)  # one independent problem per rank
-    A, B = E.discretize_zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
-    prob = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=1 + rank,
-                     elite=wl.E, sigma=wl.sigma)
-    stream = torch.cuda.Stream()
-    prob.set_stream(stream.cuda_stream)
-    x0, g = wl.start_goal()
-    x0d = torch.tensor(x0, dtype=torch.float32, device="cuda")
-    gd = torch.tensor(g, dtype=torch.float32, device="cuda")
-    kd = torch.empty(wl.m * wl.p, device="cuda")
-    cd = torch.empty(1, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
-
-    def solve_step():
-        prob.reset()
-        prob.solve_device(x0d, gd, wl.G, kd, cd)
-
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
-            solve_step()
+            step_fn()
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
@@ -221,103 +297,303 @@ def run_gpu(args, wl, rank, world, local_rank):
         for e0, e1 in ev:
             flush.zero_()
             e0.record(stream)
-            solve_step()
+            step_fn()
             e1.record(stream)
         torch.cuda.synchronize()
         t_wall1 = time.time()
         if dist:
             dist.barrier()
         clocks = sampler.stop(t_wall0, t_wall1)
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
-        if dist:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        ms_step = total_ms / args.steps
-        units = wl.P * wl.T * wl.G
-        value = units * world / (ms_step * 1e-3)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms / args.steps, clocks
 
-        # per-kernel durations, CUDA events around each launch on this stream
-        roll_us, sel_us = prob.time_generation(20)
 
-    # end to end through the public API with host buffers
-    n_e2e = max(1, min(args.e2e_steps, args.steps))
-    e2e_t = []
-    for i in range(n_e2e + 3):
+def max_over_ranks(v, dist):
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def e2e_seconds(fn, stream, flush, n):
+    import torch
+    out = []
+    for i in range(n + 3):
         with torch.cuda.stream(stream):
             flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        prob.reset()
-        prob.solve(x0, g, wl.G)
+        fn()
         if i >= 3:
-            e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+            out.append(time.perf_counter() - t0)
+    return float(np.mean(out))
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-    props = torch.cuda.get_device_properties(local_rank)
-    sms = props.multi_processor_count
+
+def fp32_peak(E, clocks, local_rank):
+    import torch
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak_derived = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
     try:
-        peak_measured = E.measure_fp32_peak()
+        measured = E.measure_fp32_peak()
     except E.EmpcError:
-        peak_measured = None
-    flops = alg_flops_per_candidate(wl) * wl.P
-    achieved = flops / (roll_us * 1e-6) / 1e12
-    tr = traffic_record("rollout.cu")
+        measured = None
+    return peak, f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz", measured
+
+
+def single_config(name):
+    cfg = {}
+    if name == "c3":
+        cfg = dict(refine_steps=5, ckpt_every=10)
+    if name == "c5":
+        cfg = dict(precision=1)
+    return cfg
+
+
+def run_gpu(args, wl, rank, world, local_rank):
+    import torch
+    import paper_2001_04931_gb300 as E
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    if args.workload == "c4":
+        line = run_batched(args, rank, world, local_rank, dist, stream, flush)
+    else:
+        line = run_single(args, rank, world, local_rank, dist, stream, flush)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_single(args, rank, world, local_rank, dist, stream, flush):
+    import torch
+    import paper_2001_04931_gb300 as E
+    wl = W.config(args.workload, seed=rank)  # one independent problem per rank
+    A, B = E.discretize_zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+    extra = single_config(wl.name)
+    prob = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=1 + rank,
+                     elite=wl.E, sigma=wl.sigma, **extra)
+    prob.set_stream(stream.cuda_stream)
+    x0, g = wl.start_goal()
+    x0d = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    gd = torch.tensor(g, dtype=torch.float32, device="cuda")
+    kd = torch.empty(wl.m * wl.p, device="cuda")
+    cd = torch.empty(1, device="cuda")
+
+    def solve_step():
+        prob.reset()
+        prob.solve_device(x0d, gd, wl.G, kd, cd)
+
+    ms_step, clocks = timed_steps(solve_step, stream, args, local_rank, dist, flush)
+    units = wl.P * wl.T * wl.G
+    value = units * world / (ms_step * 1e-3)
+    with torch.cuda.stream(stream):
+        roll_us, sel_us = prob.time_generation(10 if wl.name == "c5" else 20)
+    e2e_s = max_over_ranks(e2e_seconds(lambda: (prob.reset(), prob.solve(x0, g, wl.G)), stream,
+                                       flush, max(1, min(args.e2e_steps, args.steps))), dist)
+    if rank != 0:
+        return None
     info = prob.info()
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, args.cpu_seconds)
-    line = {
+    bf16 = wl.name == "c5"
+    if bf16:
+        peak, basis = measured_bf16_peak()
+        flops = wl.P * wl.T * 2 * wl.n * wl.n  # the A_d x contraction
+        achieved = flops / (roll_us * 1e-6) / 1e12
+        roof = {"bound": "tensor", "kernel": "rollout_bf16_kernel (tcgen05 BF16, FP32 accum)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_basis": basis, "flops_per_launch": flops,
+                "mma_flops_per_launch": wl.P * wl.T * 2 * 128 * 192,
+                "launch_us": roll_us, "select_us": sel_us, "traffic": None}
+    else:
+        peak, basis, measured = fp32_peak(E, clocks, local_rank)
+        flops = alg_flops_per_candidate(wl) * wl.P
+        achieved = flops / (roll_us * 1e-6) / 1e12
+        tr = traffic_record("rollout_warp.cuh")
+        roof = {"bound": "alu", "kernel": "rollout_warp_kernel (fused breed+rollout+cost)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_basis": basis, "measured_fp32_peak": measured,
+                "frac_of_measured": (achieved / measured) if measured else None,
+                "flops_per_launch": flops, "launch_us": roll_us, "select_us": sel_us,
+                "traffic": tr["dram_bytes_per_launch"] if tr else None}
+    compare = None
+    if wl.name == "c3":
+        compare = compare_refined(E, wl, A, B, prob, x0, g, ms_step)
+    if wl.name == "c5":
+        compare = compare_bf16(E, wl, A, B, prob, x0, g, ms_step)
+    launches = wl.G * 2 + (wl.G - 1 if wl.name == "c3" else 0)
+    cpu = None if args.no_cpu_baseline else cpu_baseline(wl, args.cpu_seconds)
+    return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "ms_per_problem": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32",
+        "vs_baseline": None, "dtype": "bf16" if bf16 else "f32",
         "data": "synthetic: seeded mass-spring-damper chain, ZOH-discretized, x0/goal U[-1,1]",
         "config": {"workload": workload_desc(wl),
                    "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write)",
-                   "tile": {"nx": info.tile_nx, "rows": info.tile_rows,
+                   "tile": {"kind": info.tile_kind, "nx": info.tile_nx, "rows": info.tile_rows,
                             "cands": info.tile_cands, "groups": info.tile_groups,
                             "threads": info.threads_per_cta, "ctas": info.ctas},
-                   "replicas": world},
-        "roofline": {"bound": "alu", "kernel": "rollout_kernel (fused breed+rollout+cost)",
-                     "achieved": achieved, "peak": peak_derived, "unit": "TFLOP/s",
-                     "frac": achieved / peak_derived,
-                     "peak_basis": f"derived: {sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                     "measured_fp32_peak": peak_measured,
-                     "frac_of_measured": (achieved / peak_measured) if peak_measured else None,
-                     "flops_per_launch": flops, "launch_us": roll_us, "select_us": sel_us,
-                     "traffic": tr["dram_bytes_per_launch"] if tr else None},
+                   "replicas": world, **({"options": extra} if extra else {})},
+        "roofline": roof,
         "e2e": {"value": units / e2e_s, "unit": UNIT, "ms_per_problem": 1e3 * e2e_s,
                 "h2d_bytes_per_step": 2 * 4 * wl.n,
                 "d2h_bytes_per_step": 4 * (wl.m * wl.p + 2)},
-        "gpu_launches": args.steps * wl.G * 2,
+        "gpu_launches": args.steps * launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        **({"compare": compare} if compare else {}),
     }
-    print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+
+
+def compare_refined(E, wl, A, B, prob, x0, g, ms_refined):
+    """Refined EMPC against plain FP32 EMPC: final costs after G generations,
+    and the generations (and time) plain EMPC needs to come within 1% of the
+    refined final cost."""
+    prob.reset()
+    _, c_ref = prob.solve(x0, g, wl.G)
+    plain = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=1, elite=wl.E,
+                      sigma=wl.sigma)
+    t0 = time.perf_counter()
+    _, c_plain = plain.solve(x0, g, wl.G)
+    ms_plain = 1e3 * (time.perf_counter() - t0)
+    plain.reset()
+    gens, best = 0, float("inf")
+    t0 = time.perf_counter()
+    while gens < 20 * wl.G and best > c_ref * 1.01:
+        _, best = plain.solve(x0, g, 1)
+        gens += 1
+    ms_match = 1e3 * (time.perf_counter() - t0)
+    plain.close()
+    return {"refined_final_cost": c_ref, "plain_final_cost": c_plain,
+            "refined_ms_per_solve": ms_refined, "plain_ms_per_solve_host": ms_plain,
+            "plain_generations_to_within_1pct": gens if best <= c_ref * 1.01 else None,
+            "plain_ms_to_within_1pct_host": ms_match if best <= c_ref * 1.01 else None}
+
+
+def compare_bf16(E, wl, A, B, prob, x0, g, ms_bf16):
+    """BF16 tensor-core EMPC against FP32 EMPC on the same GPU: solve time and
+    final best cost, both best knot vectors re-evaluated by the FP32 path."""
+    import torch
+    prob.reset()
+    k_b, _ = prob.solve(x0, g, wl.G)
+    f32 = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=1, elite=wl.E,
+                    sigma=wl.sigma)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k_f, _ = f32.solve(x0, g, wl.G)
+    ms_f32 = 1e3 * (time.perf_counter() - t0)
+    pop = torch.from_numpy(np.stack([k_b, k_f], 1).astype(np.float32)).cuda().contiguous()
+    cost = torch.empty(2, device="cuda")
+    f32.evaluate(torch.tensor(x0, dtype=torch.float32, device="cuda"),
+                 torch.tensor(g, dtype=torch.float32, device="cuda"), pop, cost)
+    torch.cuda.synchronize()
+    cb, cf = cost.cpu().numpy().tolist()
+    f32.close()
+    return {"bf16_ms_per_solve": ms_bf16, "fp32_ms_per_solve_host": ms_f32,
+            "speedup": ms_f32 / ms_bf16, "bf16_final_cost_fp32_eval": cb,
+            "fp32_final_cost": cf, "final_cost_ratio": cb / cf}
+
+
+def run_batched(args, rank, world, local_rank, dist, stream, flush):
+    import paper_2001_04931_gb300 as E
+    wls = W.batched_problems(256, seed=rank)
+    G = wls[0].G
+    probs = []
+    for wl in wls:
+        A, B = E.discretize_zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+        x0, g = wl.start_goal()
+        probs.append(dict(A=A, B=B, Q=wl.Q(), R=wl.R(), bounds=wl.bounds(), x0=x0, x_goal=g,
+                          horizon=wl.T, knots=wl.p, pop=wl.P, elite=wl.E, seed=wl.seed,
+                          sigma=wl.sigma))
+    import torch
+    bt = E.Batch(probs)
+    bt.set_stream(stream.cuda_stream)
+    info = bt.info()
+
+    def solve_step():
+        bt.reset()
+        bt.solve_device(G)
+
+    ms_step, clocks = timed_steps(solve_step, stream, args, local_rank, dist, flush)
+    units = info.state_steps_per_generation * G
+    value = units * world / (ms_step * 1e-3)
+    e2e_s = max_over_ranks(e2e_seconds(lambda: (bt.reset(), bt.solve(G)), stream, flush,
+                                       max(1, min(args.e2e_steps, args.steps))), dist)
+    if rank != 0:
+        return None
+    peak, basis, measured = fp32_peak(E, clocks, local_rank)
+    flops = sum(alg_flops_per_candidate(wl) * wl.P for wl in wls) * G
+    achieved = flops / (ms_step * 1e-3) / 1e12
+    # sequential baseline: the same problems one after another through the
+    # single-problem API (warp tiles, the same arithmetic)
+    bt.reset()
+    bk, bc = bt.solve(G)
+    seq_s, diffs = 0.0, []
+    for i, pr in enumerate(probs):
+        single = E.Problem(pr["A"], pr["B"], pr["Q"], pr["R"], pr["bounds"], pr["horizon"],
+                           pr["knots"], pr["pop"], seed=pr["seed"], elite=pr["elite"],
+                           sigma=pr["sigma"], tile=1)
+        single.solve(pr["x0"], pr["x_goal"], 1)
+        single.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, c = single.solve(pr["x0"], pr["x_goal"], G)
+        seq_s += time.perf_counter() - t0
+        diffs.append(abs(c - bc[i]) / max(abs(bc[i]), 1e-30))
+        single.close()
+    cpu = None if args.no_cpu_baseline else cpu_baseline_batch(wls, args.cpu_seconds)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "ms_per_problem": ms_step / len(wls), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: 256 seeded chains, DoF 2-32, T 20-200, P 256-4096, 3-8 knots",
+        "config": {"workload": f"c4: 256 problems, G={G}, one persistent launch per solve",
+                   "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "launch": {"ctas": info.ctas, "warps_per_cta": info.warps_per_cta,
+                              "cands_per_lane": info.cands_per_lane,
+                              "items_per_generation": info.items_per_generation},
+                   "replicas": world},
+        "roofline": {"bound": "alu", "kernel": "batched_kernel (persistent, all problems)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "peak_basis": basis,
+                     "measured_fp32_peak": measured, "flops_per_launch": flops,
+                     "launch_us": 1e3 * ms_step, "traffic": None},
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s,
+                "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * (info.total_knots + 2 * len(wls) + 1)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "compare": {"sequential_single_problem_ms": 1e3 * seq_s, "batched_ms": ms_step,
+                    "speedup": 1e3 * seq_s / ms_step,
+                    "max_final_cost_rel_diff": float(max(diffs))},
+    }
 
 
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
-    wl = W.config(args.workload)
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args, wl)
+            if args.workload == "c4":
+                run_reference_batch(args)
+            else:
+                run_reference(args, W.config(args.workload))
         return
-    run_gpu(args, wl, rank, world, local_rank)
+    run_gpu(args, None, rank, world, local_rank)
 
 
 if __name__ == "__main__":

@@ -112,8 +112,8 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
  * Writes the best knot vector (host, [m*p], parameter q = i*p + j) and its
  * cost.  u* of Algorithm 1 is best_knots[i*p + 0] for each input i.
  * Host-to-device copy of x0/x_goal, the generations, and the device-to-host
- * copy of the result all happen inside the call (the paper's EMPC solve time,
- * Sec. VI-A).  Returns EMPC_ENONFINITE if the best cost is not finite.
+ * copy of the result all happen inside the call (the EMPC solve time of the
+ * simulation experiments, Sec. VI-A).  Returns EMPC_ENONFINITE if the best cost is not finite.
  */
 empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal,
                        int generations, float* best_knots, float* best_cost);
@@ -272,6 +272,13 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
  * starts cold.  EMPC_ENONFINITE if a problem's best cost is not finite.
  */
 empc_status empc_batch_solve(empc_batch b, int generations, float* best_knots, float* best_costs);
+/* As empc_batch_solve without the copies back: asynchronous on the batch's
+ * stream (results stay on the device; read them with empc_batch_get_state).
+ * A wait that runs out is reported by the next empc_batch_solve. */
+empc_status empc_batch_solve_device(empc_batch b, int generations);
+/* Run subsequent batch work on `stream` (a cudaStream_t); NULL selects the
+ * batch's own stream. */
+empc_status empc_batch_set_stream(empc_batch b, void* stream);
 empc_status empc_batch_reset(empc_batch b);
 /* Current population [m*p][pop], costs [pop] and elites [E] of problem
  * `index` into device buffers (any may be NULL); synchronous. */

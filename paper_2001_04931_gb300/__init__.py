@@ -95,6 +95,8 @@ _SIGNATURES = {
                                ctypes.POINTER(empc_config), ctypes.POINTER(_h)]),
     "empc_batch_solve": (_i, [_h, _i, _fp, _fp]),
     "empc_batch_reset": (_i, [_h]),
+    "empc_batch_solve_device": (_i, [_h, _i]),
+    "empc_batch_set_stream": (_i, [_h, _vp]),
     "empc_batch_get_state": (_i, [_h, _i, _vp, _vp, _vp]),
     "empc_batch_get_info": (_i, [_h, ctypes.POINTER(empc_batch_info)]),
     "empc_batch_inject_stall": (_i, [_h, _i, ctypes.c_double]),
@@ -325,6 +327,13 @@ class Batch:
             out.append(knots[at:at + m * p].copy())
             at += m * p
         return out, costs
+
+    def solve_device(self, generations):
+        """Asynchronous solve on the batch's stream; results stay on the device."""
+        _bcheck(_lib.empc_batch_solve_device(self.handle, int(generations)), self.handle)
+
+    def set_stream(self, stream):
+        _bcheck(_lib.empc_batch_set_stream(self.handle, stream), self.handle)
 
     def reset(self):
         _bcheck(_lib.empc_batch_reset(self.handle), self.handle)

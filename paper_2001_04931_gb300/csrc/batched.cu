@@ -400,7 +400,8 @@ struct empc_batch_s {
     int total_knots = 0;
     double state_steps_per_gen = 0;
     int device = 0, sms = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // the batch's own stream
+    cudaStream_t run_stream = nullptr;  // where solves run (own stream unless set)
     char* arena = nullptr;
     BatchProblem* d_probs = nullptr;
     std::vector<BatchProblem> h_probs;
@@ -781,10 +782,10 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
     return EMPC_OK;
 }
 
-empc_status empc_batch_solve(empc_batch b, int generations, float* best_knots, float* best_costs) {
-    if (!b) return bfail(nullptr, EMPC_EINVAL, "NULL batch");
-    if (generations < 1 || !best_knots || !best_costs)
-        return bfail(b, EMPC_EINVAL, "need generations >= 1 and output buffers");
+namespace {
+
+// Launch `generations` generations (cached graph) on the run stream.
+empc_status batch_launch(empc_batch b, int generations) {
     const empc::GraphKeyB key{generations, b->has_pop ? 0 : 1, b->parity};
     cudaGraphExec_t exec = nullptr;
     auto it = b->graphs.find(key);
@@ -805,19 +806,43 @@ empc_status empc_batch_solve(empc_batch b, int generations, float* best_knots, f
         if (e != cudaSuccess) return bfail(b, EMPC_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
         b->graphs[key] = exec;
     }
-    EMPC_BCUDA(b, cudaGraphLaunch(exec, b->stream));
-    float* st = b->h_stage;
-    EMPC_BCUDA(b, cudaMemcpyAsync(st, b->d_best_knots, sizeof(float) * b->total_knots,
-                                  cudaMemcpyDeviceToHost, b->stream));
-    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots, b->d_best_costs, sizeof(float) * b->count,
-                                  cudaMemcpyDeviceToHost, b->stream));
-    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots + b->count, b->d_status,
-                                  sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->stream));
-    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots + 2 * b->count, b->d_error, sizeof(int),
-                                  cudaMemcpyDeviceToHost, b->stream));
-    EMPC_BCUDA(b, cudaStreamSynchronize(b->stream));
+    EMPC_BCUDA(b, cudaGraphLaunch(exec, b->run_stream ? b->run_stream : b->stream));
     b->parity ^= generations & 1;
     b->has_pop = true;
+    return EMPC_OK;
+}
+
+}  // namespace
+
+empc_status empc_batch_solve_device(empc_batch b, int generations) {
+    if (!b) return bfail(nullptr, EMPC_EINVAL, "NULL batch");
+    if (generations < 1) return bfail(b, EMPC_EINVAL, "need generations >= 1");
+    return batch_launch(b, generations);
+}
+
+empc_status empc_batch_set_stream(empc_batch b, void* stream) {
+    if (!b) return bfail(nullptr, EMPC_EINVAL, "NULL batch");
+    b->run_stream = static_cast<cudaStream_t>(stream);
+    return EMPC_OK;
+}
+
+empc_status empc_batch_solve(empc_batch b, int generations, float* best_knots, float* best_costs) {
+    if (!b) return bfail(nullptr, EMPC_EINVAL, "NULL batch");
+    if (generations < 1 || !best_knots || !best_costs)
+        return bfail(b, EMPC_EINVAL, "need generations >= 1 and output buffers");
+    empc_status ls = batch_launch(b, generations);
+    if (ls != EMPC_OK) return ls;
+    cudaStream_t rs = b->run_stream ? b->run_stream : b->stream;
+    float* st = b->h_stage;
+    EMPC_BCUDA(b, cudaMemcpyAsync(st, b->d_best_knots, sizeof(float) * b->total_knots,
+                                  cudaMemcpyDeviceToHost, rs));
+    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots, b->d_best_costs, sizeof(float) * b->count,
+                                  cudaMemcpyDeviceToHost, rs));
+    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots + b->count, b->d_status,
+                                  sizeof(int) * b->count, cudaMemcpyDeviceToHost, rs));
+    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots + 2 * b->count, b->d_error, sizeof(int),
+                                  cudaMemcpyDeviceToHost, rs));
+    EMPC_BCUDA(b, cudaStreamSynchronize(rs));
     int errflag;
     std::memcpy(&errflag, st + b->total_knots + 2 * b->count, sizeof(int));
     if (errflag) {
@@ -847,16 +872,17 @@ empc_status empc_batch_get_state(empc_batch b, int index, float* dev_pop, float*
     if (!b->has_pop) return bfail(b, EMPC_ESTATE, "no population yet (solve first)");
     const BatchProblem& bp = b->h_probs[index];
     const size_t DP = (size_t)b->D[index] * b->P[index];
+    cudaStream_t rs = b->run_stream ? b->run_stream : b->stream;
     if (dev_pop)
         EMPC_BCUDA(b, cudaMemcpyAsync(dev_pop, bp.pop[b->parity], sizeof(float) * DP,
-                                      cudaMemcpyDeviceToDevice, b->stream));
+                                      cudaMemcpyDeviceToDevice, rs));
     if (dev_cost)
         EMPC_BCUDA(b, cudaMemcpyAsync(dev_cost, bp.a.cost, sizeof(float) * b->P[index],
-                                      cudaMemcpyDeviceToDevice, b->stream));
+                                      cudaMemcpyDeviceToDevice, rs));
     if (dev_elite)
         EMPC_BCUDA(b, cudaMemcpyAsync(dev_elite, bp.a.elite_idx, sizeof(int) * b->E[index],
-                                      cudaMemcpyDeviceToDevice, b->stream));
-    EMPC_BCUDA(b, cudaStreamSynchronize(b->stream));
+                                      cudaMemcpyDeviceToDevice, rs));
+    EMPC_BCUDA(b, cudaStreamSynchronize(rs));
     return EMPC_OK;
 }
 

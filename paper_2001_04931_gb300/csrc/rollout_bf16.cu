@@ -305,13 +305,14 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         if (!__syncthreads_and(ok)) break;  // every thread leaves together
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(Acur), b0 = smem_u32(sB);
+            // descriptors advance by (byte offset >> 4) in their start-address field
+            const uint64_t ad0 = sdesc(smem_u32(Acur)), bd0 = sdesc(smem_u32(sB));
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
 #pragma unroll
                 for (int kk = 0; kk < kK / 16; ++kk) {
-                    const uint32_t off = (kk >> 2) * kAtomBytes + (kk & 3) * 32;
-                    mma_bf16(tmem + h * 64, sdesc(a0 + off), sdesc(b0 + off + h * 64 * 128), idesc,
+                    const uint32_t off = ((kk >> 2) * kAtomBytes + (kk & 3) * 32) >> 4;
+                    mma_bf16(tmem + h * 64, ad0 + off, bd0 + off + ((h * 64 * 128) >> 4), idesc,
                              kk > 0 ? 1u : 0u);
                 }
                 mma_commit(&mbar[h]);
@@ -326,20 +327,23 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
             continue;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float y[2][32];
+        tmem_ld32(lane_base + (2 * grp) * 32, y[0]);
+        tmem_ld32(lane_base + (2 * grp + 1) * 32, y[1]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int c2 = 0; c2 < 2; ++c2) {
             const int ch = 2 * grp + c2;
-            float y[32];
-            tmem_ld32(lane_base + ch * 32, y);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const float4* g4 = reinterpret_cast<const float4*>(sg + ch * 32);
             const float4* q4 = reinterpret_cast<const float4*>(sq + ch * 32);
 #pragma unroll
             for (int j = 0; j < 32; j += 4) {
                 const int jj = c2 * 32 + j;
                 const float4 gg = g4[j / 4], qq = q4[j / 4];
-                const float2 x01 = add2(make_float2(xs[jj], xs[jj + 1]), make_float2(y[j], y[j + 1]));
-                const float2 x23 = add2(make_float2(xs[jj + 2], xs[jj + 3]), make_float2(y[j + 2], y[j + 3]));
+                const float2 x01 = add2(make_float2(xs[jj], xs[jj + 1]),
+                                        make_float2(y[c2][j], y[c2][j + 1]));
+                const float2 x23 = add2(make_float2(xs[jj + 2], xs[jj + 3]),
+                                        make_float2(y[c2][j + 2], y[c2][j + 3]));
                 xs[jj] = x01.x; xs[jj + 1] = x01.y; xs[jj + 2] = x23.x; xs[jj + 3] = x23.y;
                 const float2 e01 = add2(x01, make_float2(-gg.x, -gg.y));
                 const float2 e23 = add2(x23, make_float2(-gg.z, -gg.w));

@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="1-based rollout tile shape to force (0: autotune); profiling "
+                         "runs use it so that the profiled launches match a plain run")
     return ap.parse_args()
 
 
@@ -304,21 +307,23 @@ def timed_steps(step_fn, stream, args, local_rank, dist, flush):
         if dist:
             dist.barrier()
         clocks = sampler.stop(t_wall0, t_wall1)
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist)
     return total_ms / args.steps, clocks
 
 
-def max_over_ranks(v, dist):
+def max_over_ranks(v, dist, device="cuda"):
+    """The largest of the ranks' values (the slowest replica sets the time)."""
     if not dist:
         return v
     import torch
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    t = torch.tensor([v], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all replicas processed per second of the slowest replica."""
+    return units_per_rank * world / seconds
 
 
 def e2e_seconds(fn, stream, flush, n):
@@ -383,6 +388,8 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
     wl = W.config(args.workload, seed=rank)  # one independent problem per rank
     A, B = E.discretize_zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
     extra = single_config(wl.name)
+    if args.tile:
+        extra["tile"] = args.tile
     prob = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=1 + rank,
                      elite=wl.E, sigma=wl.sigma, **extra)
     prob.set_stream(stream.cuda_stream)
@@ -398,7 +405,7 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
 
     ms_step, clocks = timed_steps(solve_step, stream, args, local_rank, dist, flush)
     units = wl.P * wl.T * wl.G
-    value = units * world / (ms_step * 1e-3)
+    value = whole_job_rate(units, world, ms_step * 1e-3)
     with torch.cuda.stream(stream):
         roll_us, sel_us = prob.time_generation(10 if wl.name == "c5" else 20)
     e2e_s = max_over_ranks(e2e_seconds(lambda: (prob.reset(), prob.solve(x0, g, wl.G)), stream,
@@ -447,7 +454,7 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                             "threads": info.threads_per_cta, "ctas": info.ctas},
                    "replicas": world, **({"options": extra} if extra else {})},
         "roofline": roof,
-        "e2e": {"value": units / e2e_s, "unit": UNIT, "ms_per_problem": 1e3 * e2e_s,
+        "e2e": {"value": whole_job_rate(units, world, e2e_s), "unit": UNIT, "ms_per_problem": 1e3 * e2e_s,
                 "h2d_bytes_per_step": 2 * 4 * wl.n,
                 "d2h_bytes_per_step": 4 * (wl.m * wl.p + 2)},
         "gpu_launches": args.steps * launches,
@@ -528,30 +535,39 @@ def run_batched(args, rank, world, local_rank, dist, stream, flush):
 
     ms_step, clocks = timed_steps(solve_step, stream, args, local_rank, dist, flush)
     units = info.state_steps_per_generation * G
-    value = units * world / (ms_step * 1e-3)
-    e2e_s = max_over_ranks(e2e_seconds(lambda: (bt.reset(), bt.solve(G)), stream, flush,
+    value = whole_job_rate(units, world, ms_step * 1e-3)
+    # end to end: every step uploads all problems' start states and goals
+    # (FP64 host arrays, one transfer) and reads every best plan back
+    x0s = [pr["x0"] for pr in probs]
+    goals = [pr["x_goal"] for pr in probs]
+    e2e_s = max_over_ranks(e2e_seconds(lambda: (bt.reset(), bt.set_targets(x0s, goals),
+                                                bt.solve(G)), stream, flush,
                                        max(1, min(args.e2e_steps, args.steps))), dist)
+    h2d = info.h2d_bytes_targets
     if rank != 0:
         return None
     peak, basis, measured = fp32_peak(E, clocks, local_rank)
     flops = sum(alg_flops_per_candidate(wl) * wl.P for wl in wls) * G
     achieved = flops / (ms_step * 1e-3) / 1e12
     # sequential baseline: the same problems one after another through the
-    # single-problem API (warp tiles, the same arithmetic)
-    bt.reset()
-    bk, bc = bt.solve(G)
+    # single-problem API, each with its own autotuned tile.  A fresh batch and
+    # a fresh handle both start at generation 0, so their first solves draw
+    # the same numbers; the timed single solve is the second (graph cached).
+    bt0 = E.Batch(probs)
+    bk, bc = bt0.solve(G)
+    bt0.close()
     seq_s, diffs = 0.0, []
     for i, pr in enumerate(probs):
         single = E.Problem(pr["A"], pr["B"], pr["Q"], pr["R"], pr["bounds"], pr["horizon"],
                            pr["knots"], pr["pop"], seed=pr["seed"], elite=pr["elite"],
-                           sigma=pr["sigma"], tile=1)
-        single.solve(pr["x0"], pr["x_goal"], 1)
+                           sigma=pr["sigma"])
+        _, c = single.solve(pr["x0"], pr["x_goal"], G)
+        diffs.append(abs(c - bc[i]) / max(abs(bc[i]), 1e-30))
         single.reset()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, c = single.solve(pr["x0"], pr["x_goal"], G)
+        single.solve(pr["x0"], pr["x_goal"], G)
         seq_s += time.perf_counter() - t0
-        diffs.append(abs(c - bc[i]) / max(abs(bc[i]), 1e-30))
         single.close()
     cpu = None if args.no_cpu_baseline else cpu_baseline_batch(wls, args.cpu_seconds)
     return {
@@ -571,9 +587,9 @@ def run_batched(args, rank, world, local_rank, dist, stream, flush):
                      "frac": achieved / peak, "peak_basis": basis,
                      "measured_fp32_peak": measured, "flops_per_launch": flops,
                      "launch_us": 1e3 * ms_step, "traffic": None},
-        "e2e": {"value": units / e2e_s, "unit": UNIT, "ms_per_step": 1e3 * e2e_s,
-                "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 4 * (info.total_knots + 2 * len(wls) + 1)},
+        "e2e": {"value": whole_job_rate(units, world, e2e_s), "unit": UNIT, "ms_per_step": 1e3 * e2e_s,
+                "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": info.d2h_bytes_solve},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,

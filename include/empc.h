@@ -250,6 +250,8 @@ typedef struct {
     int ctas, warps_per_cta, cands_per_lane, items_per_generation;
     double state_steps_per_generation;  /* sum over problems of pop * horizon */
     float tuned_us;                     /* autotuned cold generation of the whole batch */
+    int h2d_bytes_targets;              /* bytes one empc_batch_set_targets transfers */
+    int d2h_bytes_solve;                /* bytes one empc_batch_solve reads back */
 } empc_batch_info;
 
 /*
@@ -279,6 +281,16 @@ empc_status empc_batch_solve_device(empc_batch b, int generations);
 /* Run subsequent batch work on `stream` (a cudaStream_t); NULL selects the
  * batch's own stream. */
 empc_status empc_batch_set_stream(empc_batch b, void* stream);
+/*
+ * empc_batch_set_targets - new start states and goals for every problem, as in
+ * a receding-horizon step where each problem's x0 is the measured state
+ * (Sec. III-A).  x0 and x_goal are host FP64, the problems' vectors
+ * concatenated in order ([n_i] each); both are copied (rounded to FP32) to the
+ * device on the batch's stream in one transfer and used from the next
+ * generation on.  Populations are kept, so the next solve warm-starts from
+ * the previous plan.  EMPC_EINVAL on NULL or non-finite input.
+ */
+empc_status empc_batch_set_targets(empc_batch b, const double* x0, const double* x_goal);
 empc_status empc_batch_reset(empc_batch b);
 /* Current population [m*p][pop], costs [pop] and elites [E] of problem
  * `index` into device buffers (any may be NULL); synchronous. */

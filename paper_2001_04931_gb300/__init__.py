@@ -61,7 +61,8 @@ class empc_batch_info(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("total_knots", ctypes.c_int), ("ctas", ctypes.c_int),
                 ("warps_per_cta", ctypes.c_int), ("cands_per_lane", ctypes.c_int),
                 ("items_per_generation", ctypes.c_int),
-                ("state_steps_per_generation", ctypes.c_double), ("tuned_us", ctypes.c_float)]
+                ("state_steps_per_generation", ctypes.c_double), ("tuned_us", ctypes.c_float),
+                ("h2d_bytes_targets", ctypes.c_int), ("d2h_bytes_solve", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -95,6 +96,7 @@ _SIGNATURES = {
                                ctypes.POINTER(empc_config), ctypes.POINTER(_h)]),
     "empc_batch_solve": (_i, [_h, _i, _fp, _fp]),
     "empc_batch_reset": (_i, [_h]),
+    "empc_batch_set_targets": (_i, [_h, _dp, _dp]),
     "empc_batch_solve_device": (_i, [_h, _i]),
     "empc_batch_set_stream": (_i, [_h, _vp]),
     "empc_batch_get_state": (_i, [_h, _i, _vp, _vp, _vp]),
@@ -337,6 +339,16 @@ class Batch:
 
     def reset(self):
         _bcheck(_lib.empc_batch_reset(self.handle), self.handle)
+
+    def set_targets(self, x0s, goals):
+        """New start states and goals (one array per problem), used from the
+        next generation on; the populations are kept."""
+        x = np.ascontiguousarray(np.concatenate([np.ravel(v) for v in x0s]), np.float64)
+        g = np.ascontiguousarray(np.concatenate([np.ravel(v) for v in goals]), np.float64)
+        if x.size != sum(d[0] for d in self.dims) or g.size != x.size:
+            raise ValueError("need one x0 and one goal of length n per problem")
+        _bcheck(_lib.empc_batch_set_targets(self.handle, x.ctypes.data_as(_dp),
+                                            g.ctypes.data_as(_dp)), self.handle)
 
     def get_state(self, index, pop=None, cost=None, elite=None):
         _bcheck(_lib.empc_batch_get_state(self.handle, int(index), _dev(pop), _dev(cost),

@@ -412,7 +412,14 @@ struct empc_batch_s {
     float* d_best_knots = nullptr;   // [total_knots]
     float* d_best_costs = nullptr;   // [count]
     int* d_status = nullptr;         // [count]
-    float* h_stage = nullptr;        // pinned: knots | costs | status | error
+    float* h_stage = nullptr;        // pinned image of the result span (knots .. error)
+    size_t result_floats = 0;        // floats from the best knots to the error word
+    size_t off_costs_rel = 0, off_status_rel = 0, off_error_rel = 0;  // within that span
+    std::vector<int> tgt_off;        // problem's offset in the x0 / goal blocks
+    size_t tgt_floats = 0;           // floats of one block (x0 block, then goal block)
+    float* d_targets = nullptr;      // device: x0 block | goal block
+    float* h_targets = nullptr;      // pinned staging of the same
+    cudaEvent_t tgt_done = nullptr;  // the last targets copy has read h_targets
     int shape = 0, grid = 0;
     size_t smem = 0;
     int bt_floats = 0, ks_floats = 0, slice_floats[2] = {0, 0}, key_words = 0, sel_cap = 0;
@@ -445,6 +452,8 @@ void free_batch(empc_batch b) {
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->arena) cudaFree(b->arena);
     if (b->h_stage) cudaFreeHost(b->h_stage);
+    if (b->h_targets) cudaFreeHost(b->h_targets);
+    if (b->tgt_done) cudaEventDestroy(b->tgt_done);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -534,7 +543,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         return at;
     };
     struct Off {
-        size_t D, BT, qd, rd, gram, ks, lo, hi, x0, goal, pop0, pop1, cost, elite, ecost, gen, status;
+        size_t D, BT, qd, rd, gram, ks, lo, hi, pop0, pop1, cost, elite, ecost, gen, status;
     };
     std::vector<Off> off(count);
     for (int i = 0; i < count; ++i) {
@@ -581,8 +590,9 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         o.ks = reserve(4 * (size_t)d.horizon);
         o.lo = reserve(d.m);
         o.hi = reserve(d.m);
-        o.x0 = reserve(d.n);
-        o.goal = reserve(d.n);
+        // start and goal live in two contiguous blocks (one copy updates all)
+        b->tgt_off.push_back((int)b->tgt_floats);
+        b->tgt_floats += (size_t)(d.n + 3) / 4 * 4;
         o.pop0 = reserve(DP);
         o.pop1 = reserve(DP);
         o.cost = reserve(d.pop);
@@ -591,6 +601,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         o.gen = reserve(1);
         o.status = reserve(1);
     }
+    const size_t off_tgt = reserve(2 * b->tgt_floats);
     const size_t off_best = reserve(b->total_knots);
     const size_t off_bcost = reserve(count);
     const size_t off_bstat = reserve(count);
@@ -647,8 +658,14 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaStreamCreate(&b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->arena, floats * sizeof(float));
-    if (e == cudaSuccess)
-        e = cudaMallocHost(&b->h_stage, sizeof(float) * ((size_t)b->total_knots + 2 * (size_t)count + 1));
+    b->result_floats = off_error + 1 - off_best;
+    b->off_costs_rel = off_bcost - off_best;
+    b->off_status_rel = off_bstat - off_best;
+    b->off_error_rel = off_error - off_best;
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_stage, sizeof(float) * b->result_floats);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_targets, sizeof(float) * 2 * b->tgt_floats);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tgt_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) std::memset(b->h_targets, 0, sizeof(float) * 2 * b->tgt_floats);
     if (e != cudaSuccess) {
         free_batch(b);
         return bfail(nullptr, EMPC_ECUDA, std::string("batch allocation: ") + cudaGetErrorString(e));
@@ -668,8 +685,8 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         put(o.lo, t.lo.data(), sizeof(float) * t.lo.size());
         put(o.hi, t.hi.data(), sizeof(float) * t.hi.size());
         for (int k = 0; k < d.n; ++k) {
-            img[o.x0 + k] = (float)d.x0[k];
-            img[o.goal + k] = (float)d.x_goal[k];
+            img[off_tgt + b->tgt_off[i] + k] = (float)d.x0[k];
+            img[off_tgt + b->tgt_floats + b->tgt_off[i] + k] = (float)d.x_goal[k];
         }
         BatchProblem& bp = b->h_probs[i];
         std::memset(&bp, 0, sizeof(bp));
@@ -680,8 +697,8 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         a.rdiag = base + o.rd;
         a.gram = base + o.gram;
         a.ktab = reinterpret_cast<const empc::KnotStep*>(base + o.ks);
-        a.x0 = base + o.x0;
-        a.goal = base + o.goal;
+        a.x0 = base + off_tgt + b->tgt_off[i];
+        a.goal = base + off_tgt + b->tgt_floats + b->tgt_off[i];
         a.umin = base + o.lo;
         a.umax = base + o.hi;
         a.n = d.n;
@@ -706,6 +723,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         bp.status = reinterpret_cast<int*>(base + off_bstat + i);
         bp.nx = b->nx[i];
     }
+    b->d_targets = base + off_tgt;
     b->d_probs = reinterpret_cast<BatchProblem*>(base + off_probs);
     b->d_counters = reinterpret_cast<unsigned*>(base + off_counters);
     b->d_error = reinterpret_cast<int*>(base + off_error);
@@ -834,28 +852,50 @@ empc_status empc_batch_solve(empc_batch b, int generations, float* best_knots, f
     if (ls != EMPC_OK) return ls;
     cudaStream_t rs = b->run_stream ? b->run_stream : b->stream;
     float* st = b->h_stage;
-    EMPC_BCUDA(b, cudaMemcpyAsync(st, b->d_best_knots, sizeof(float) * b->total_knots,
-                                  cudaMemcpyDeviceToHost, rs));
-    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots, b->d_best_costs, sizeof(float) * b->count,
-                                  cudaMemcpyDeviceToHost, rs));
-    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots + b->count, b->d_status,
-                                  sizeof(int) * b->count, cudaMemcpyDeviceToHost, rs));
-    EMPC_BCUDA(b, cudaMemcpyAsync(st + b->total_knots + 2 * b->count, b->d_error, sizeof(int),
+    // best knots, best costs, statuses and the error word are one span of the arena
+    EMPC_BCUDA(b, cudaMemcpyAsync(st, b->d_best_knots, sizeof(float) * b->result_floats,
                                   cudaMemcpyDeviceToHost, rs));
     EMPC_BCUDA(b, cudaStreamSynchronize(rs));
     int errflag;
-    std::memcpy(&errflag, st + b->total_knots + 2 * b->count, sizeof(int));
+    std::memcpy(&errflag, st + b->off_error_rel, sizeof(int));
     if (errflag) {
         b->has_pop = false;  // populations of an interrupted launch are not usable
         return bfail(b, EMPC_ETIMEOUT, "a batched wait ran out of time");
     }
     std::memcpy(best_knots, st, sizeof(float) * b->total_knots);
-    std::memcpy(best_costs, st + b->total_knots, sizeof(float) * b->count);
+    std::memcpy(best_costs, st + b->off_costs_rel, sizeof(float) * b->count);
     for (int i = 0; i < b->count; ++i) {
         int sbits;
-        std::memcpy(&sbits, st + b->total_knots + b->count + i, sizeof(int));
+        std::memcpy(&sbits, st + b->off_status_rel + i, sizeof(int));
         if (sbits & 1) return bfail(b, EMPC_ENONFINITE, "problem " + std::to_string(i) + ": best cost is not finite");
     }
+    return EMPC_OK;
+}
+
+empc_status empc_batch_set_targets(empc_batch b, const double* x0, const double* x_goal) {
+    if (!b) return bfail(nullptr, EMPC_EINVAL, "NULL batch");
+    if (!x0 || !x_goal) return bfail(b, EMPC_EINVAL, "NULL x0 / x_goal");
+    size_t total = 0;
+    for (int i = 0; i < b->count; ++i) total += (size_t)b->n[i];
+    if (!empc::all_finite(x0, total) || !empc::all_finite(x_goal, total))
+        return bfail(b, EMPC_EINVAL, "non-finite x0 / x_goal");
+    // the previous copy must have read the staging buffer before it is rewritten
+    EMPC_BCUDA(b, cudaEventSynchronize(b->tgt_done));
+    float* h = b->h_targets;
+    size_t at = 0;
+    for (int i = 0; i < b->count; ++i) {
+        float* hx = h + b->tgt_off[i];
+        float* hg = h + b->tgt_floats + b->tgt_off[i];
+        for (int k = 0; k < b->n[i]; ++k) {
+            hx[k] = (float)x0[at + k];
+            hg[k] = (float)x_goal[at + k];
+        }
+        at += (size_t)b->n[i];
+    }
+    cudaStream_t rs = b->run_stream ? b->run_stream : b->stream;
+    EMPC_BCUDA(b, cudaMemcpyAsync(b->d_targets, h, sizeof(float) * 2 * b->tgt_floats,
+                                  cudaMemcpyHostToDevice, rs));
+    EMPC_BCUDA(b, cudaEventRecord(b->tgt_done, rs));
     return EMPC_OK;
 }
 
@@ -897,6 +937,8 @@ empc_status empc_batch_get_info(empc_batch b, empc_batch_info* info) {
     info->items_per_generation = b->n_items[b->shape];
     info->state_steps_per_generation = b->state_steps_per_gen;
     info->tuned_us = b->tuned_us;
+    info->h2d_bytes_targets = (int)(sizeof(float) * 2 * b->tgt_floats);
+    info->d2h_bytes_solve = (int)(sizeof(float) * b->result_floats);
     return EMPC_OK;
 }
 

@@ -96,3 +96,36 @@ def test_batched_wait_runs_out_and_reports_timeout():
     knots, costs = bt.solve(2)
     assert np.isfinite(costs).all()
     bt.close()
+
+
+def test_batched_new_targets_warm_start_matches_single_problems():
+    """A receding-horizon step: new start states and goals, populations kept.
+    Each problem must follow the single-problem API given the same sequence of
+    (x0, goal) pairs, bit for bit."""
+    import paper_2001_04931_gb300 as E
+    wls = _small_batch()
+    probs = _problems(wls)
+    rng = np.random.default_rng(7)
+    x1 = [rng.uniform(-1, 1, pr["A"].shape[0]) for pr in probs]
+    g1 = [rng.uniform(-1, 1, pr["A"].shape[0]) for pr in probs]
+    bt = E.Batch(probs)
+    bt.solve(2)
+    bt.set_targets(x1, g1)
+    bk, bc = bt.solve(3)
+    for i, pr in enumerate(probs):
+        single = E.Problem(pr["A"], pr["B"], pr["Q"], pr["R"], pr["bounds"], pr["horizon"],
+                           pr["knots"], pr["pop"], seed=pr["seed"], elite=pr["elite"],
+                           sigma=pr["sigma"], tile=1)
+        single.solve(pr["x0"], pr["x_goal"], 2)
+        k, c = single.solve(x1[i], g1[i], 3)
+        assert c == bc[i]
+        np.testing.assert_array_equal(k, bk[i])
+        single.close()
+    with pytest.raises(ValueError):
+        bt.set_targets(x1[:-1], g1[:-1])
+    bad = [v.copy() for v in x1]
+    bad[0][0] = np.nan
+    with pytest.raises(E.EmpcError) as ei:
+        bt.set_targets(bad, g1)
+    assert ei.value.status == E.EMPC_EINVAL
+    bt.close()

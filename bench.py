@@ -407,7 +407,7 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
     units = wl.P * wl.T * wl.G
     value = whole_job_rate(units, world, ms_step * 1e-3)
     with torch.cuda.stream(stream):
-        roll_us, sel_us = prob.time_generation(10 if wl.name == "c5" else 20)
+        breed_us, roll_us, sel_us = prob.time_generation(10 if wl.name == "c5" else 20)
     e2e_s = max_over_ranks(e2e_seconds(lambda: (prob.reset(), prob.solve(x0, g, wl.G)), stream,
                                        flush, max(1, min(args.e2e_steps, args.steps))), dist)
     if rank != 0:
@@ -422,24 +422,27 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": basis, "flops_per_launch": flops,
                 "mma_flops_per_launch": wl.P * wl.T * 2 * 128 * 192,
-                "launch_us": roll_us, "select_us": sel_us, "traffic": None}
+                "launch_us": roll_us, "breed_us": breed_us, "select_us": sel_us,
+                "traffic": None}
     else:
         peak, basis, measured = fp32_peak(E, clocks, local_rank)
         flops = alg_flops_per_candidate(wl) * wl.P
         achieved = flops / (roll_us * 1e-6) / 1e12
         tr = traffic_record("rollout_warp.cuh")
-        roof = {"bound": "alu", "kernel": "rollout_warp_kernel (fused breed+rollout+cost)",
+        roof = {"bound": "alu", "kernel": "rollout_warp_kernel (knot expansion+rollout+cost)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": basis, "measured_fp32_peak": measured,
                 "frac_of_measured": (achieved / measured) if measured else None,
-                "flops_per_launch": flops, "launch_us": roll_us, "select_us": sel_us,
+                "flops_per_launch": flops, "launch_us": roll_us, "breed_us": breed_us,
+                "select_us": sel_us,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None}
     compare = None
     if wl.name == "c3":
         compare = compare_refined(E, wl, A, B, prob, x0, g, ms_step)
     if wl.name == "c5":
         compare = compare_bf16(E, wl, A, B, prob, x0, g, ms_step)
-    launches = wl.G * 2 + (wl.G - 1 if wl.name == "c3" else 0)
+    # per generation: breed, rollout, select (+ the refinement kernel after the first)
+    launches = wl.G * 3 + (wl.G - 1 if wl.name == "c3" else 0)
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl, args.cpu_seconds)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -202,12 +202,13 @@ empc_status empc_get_info(empc_handle h, empc_info* info);
 /*
  * empc_time_generation - measurement aid (no counterpart in the paper): run
  * `reps` warm generations as plain launches on the handle's stream and
- * report the average duration of the fused breed+rollout+cost kernel and of
- * the elite-selection kernel, from CUDA events around each launch.  The
- * generations are real (the population advances).  EMPC_ESTATE before the
- * first solve.  Synchronizes the stream.
+ * report the average duration of the fused crossover + mutation kernel, of
+ * the rollout + cost kernel and of the elite-selection kernel, from CUDA
+ * events around each launch.  The generations are real (the population
+ * advances).  EMPC_ESTATE before the first solve.  Synchronizes the stream.
  */
-empc_status empc_time_generation(empc_handle h, int reps, float* rollout_us, float* select_us);
+empc_status empc_time_generation(empc_handle h, int reps, float* breed_us, float* rollout_us,
+                                 float* select_us);
 
 /*
  * empc_measure_fp32_peak - measurement aid (no counterpart in the paper):

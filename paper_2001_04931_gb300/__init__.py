@@ -88,7 +88,7 @@ _SIGNATURES = {
     "empc_destroy": (None, [_h]),
     "empc_last_error": (ctypes.c_char_p, [_h]),
     "empc_discretize_zoh": (_i, [_dp, _dp, _i, _i, ctypes.c_double, _dp, _dp]),
-    "empc_time_generation": (_i, [_h, _i, _fp, _fp]),
+    "empc_time_generation": (_i, [_h, _i, _fp, _fp, _fp]),
     "empc_measure_fp32_peak": (_i, [_dp]),
     "empc_evaluate_noalloc": (_i, [_dp, _dp, _dp, _dp, _i, _i, _i, _i, _vp, _vp, _vp, _i,
                                   _vp, _vp]),
@@ -257,11 +257,11 @@ class Problem:
         check(_lib.empc_reset(self.handle), self.handle)
 
     def time_generation(self, reps):
-        """Average (rollout_us, select_us) of `reps` warm generations."""
-        a, b = ctypes.c_float(), ctypes.c_float()
-        check(_lib.empc_time_generation(self.handle, int(reps), ctypes.byref(a),
-                                        ctypes.byref(b)), self.handle)
-        return a.value, b.value
+        """Average (breed_us, rollout_us, select_us) of `reps` warm generations."""
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        check(_lib.empc_time_generation(self.handle, int(reps), ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c)), self.handle)
+        return a.value, b.value, c.value
 
     def set_stream(self, stream):
         check(_lib.empc_set_stream(self.handle, stream), self.handle)

@@ -147,11 +147,13 @@ empc::GradArgs grad_args(empc_handle h) {
     return g;
 }
 
-// One generation into pop[parity^1], then elite selection.  Cold: breed +
-// rollout + cost of every candidate.  Warm: the children (slots E..P-1) are
-// bred from the previous elites and rolled out; with refinement enabled the
-// elites themselves are refined by projected gradient on a second stream at
-// the same time and written, with their costs, to slots 0..E-1.
+// One generation into pop[parity^1], then elite selection.  Cold: draw every
+// candidate, then roll out and cost them.  Warm: the fused crossover +
+// mutation kernel breeds the children (slots E..P-1) from the previous
+// elites and copies the elites, then the rollout kernel evaluates them; with
+// refinement enabled the elites themselves are refined by projected gradient
+// on a second stream at the same time and written, with their costs, to
+// slots 0..E-1.
 cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_t st) {
     RolloutArgs a = base_args(h);
     a.mode = cold ? empc::kCold : empc::kWarm;
@@ -181,6 +183,10 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
     // Programmatic dependent launch between the generation's kernels (not
     // across the refinement fork/join).
     a.pdl = refine ? 0 : 1;
+    e = empc::launch_breed(a, st);
+    if (e != cudaSuccess) return e;
+    a.mode = empc::kEval;  // the rollout reads the bred population
+    a.pop_in = h->pop[parity ^ 1];
     e = empc::launch_rollout(a, h->shape, st);
     if (e != cudaSuccess) return e;
     if (refine && (e = cudaStreamWaitEvent(st, h->ev_join, 0)) != cudaSuccess) return e;
@@ -299,25 +305,26 @@ empc_status run_generations(empc_handle h, int G) {
 }
 
 empc_status autotune(empc_handle h) {
-    TileShape buf[128];
-    const int ns = std::min(empc::rollout_shapes(h->n, buf, 128), 128);
-    std::vector<TileShape> shapes(buf, buf + ns);
     std::vector<TileShape> ok;
-    for (const TileShape& s : shapes)
-        if (empc::rollout_shape_supported(s, h->n, h->m, h->p, h->T)) ok.push_back(s);
+    if (h->cfg.precision == EMPC_BF16) {
+        // tensor-core tile: the product issued as 1, 2 or 4 MMA groups
+        for (int g : {1, 2, 4}) ok.push_back(TileShape{2, 128, 1, 1, g});
+    } else {
+        TileShape buf[128];
+        const int ns = std::min(empc::rollout_shapes(h->n, buf, 128), 128);
+        for (int i = 0; i < ns; ++i)
+            if (empc::rollout_shape_supported(buf[i], h->n, h->m, h->p, h->T)) ok.push_back(buf[i]);
+    }
     if (ok.empty()) return fail(h, EMPC_EUNSUPPORTED, "no rollout tile fits this problem");
-    // score a cold-start population of the real size
+    // score the rollout of a cold-drawn population of the real size
     RolloutArgs a = base_args(h);
     a.mode = empc::kCold;
     a.pop_out = h->pop[0];
     a.cost = h->cost;
     a.gen = nullptr;
-    if (h->cfg.precision == EMPC_BF16) {
-        h->shape = TileShape{2, 128, 1, 1, 1};
-        EMPC_CUDA(h, empc::launch_rollout(a, h->shape, h->stream));
-        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
-        return EMPC_OK;
-    }
+    EMPC_CUDA(h, empc::launch_breed(a, h->stream));
+    a.mode = empc::kEval;
+    a.pop_in = h->pop[0];
     if (h->cfg.tile > 0) {
         const size_t k = (size_t)(h->cfg.tile - 1);
         if (k >= ok.size()) return fail(h, EMPC_EINVAL, "cfg.tile out of range");
@@ -794,13 +801,14 @@ empc_status empc_get_info(empc_handle h, empc_info* info) {
     return EMPC_OK;
 }
 
-empc_status empc_time_generation(empc_handle h, int reps, float* rollout_us, float* select_us) {
-    if (!h || !rollout_us || !select_us || reps < 1)
-        return fail(h, EMPC_EINVAL, "need a handle, reps >= 1 and two outputs");
+empc_status empc_time_generation(empc_handle h, int reps, float* breed_us, float* rollout_us,
+                                 float* select_us) {
+    if (!h || !breed_us || !rollout_us || !select_us || reps < 1)
+        return fail(h, EMPC_EINVAL, "need a handle, reps >= 1 and three outputs");
     if (!h->has_pop) return fail(h, EMPC_ESTATE, "no population yet (solve first)");
-    cudaEvent_t ev[3];
+    cudaEvent_t ev[4];
     for (auto& e : ev) EMPC_CUDA(h, cudaEventCreate(&e));
-    double t_roll = 0.0, t_sel = 0.0;
+    double t_breed = 0.0, t_roll = 0.0, t_sel = 0.0;
     empc_status s = EMPC_OK;
     for (int r = 0; r < reps && s == EMPC_OK; ++r) {
         RolloutArgs a = base_args(h);
@@ -810,28 +818,35 @@ empc_status empc_time_generation(empc_handle h, int reps, float* rollout_us, flo
         a.cost = h->cost;
         a.elite_idx = h->elite_idx;
         cudaError_t e = cudaEventRecord(ev[0], h->stream);
-        if (e == cudaSuccess) e = empc::launch_rollout(a, h->shape, h->stream);
+        if (e == cudaSuccess) e = empc::launch_breed(a, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+        a.mode = empc::kEval;
+        a.pop_in = h->pop[h->cur ^ 1];
+        if (e == cudaSuccess) e = empc::launch_rollout(a, h->shape, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess)
             e = empc::launch_select(h->cost, h->P, h->E, h->pop[h->cur ^ 1], h->D, h->elite_idx,
                                     h->elite_cost, h->best_knots, h->best_cost, h->gen,
                                     h->status, h->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
         if (e != cudaSuccess) {
             s = cuda_fail(h, e, "empc_time_generation");
             break;
         }
-        float a_ms = 0, b_ms = 0;
-        cudaEventElapsedTime(&a_ms, ev[0], ev[1]);
-        cudaEventElapsedTime(&b_ms, ev[1], ev[2]);
-        t_roll += a_ms;
-        t_sel += b_ms;
+        float b_ms = 0, r_ms = 0, s_ms = 0;
+        cudaEventElapsedTime(&b_ms, ev[0], ev[1]);
+        cudaEventElapsedTime(&r_ms, ev[1], ev[2]);
+        cudaEventElapsedTime(&s_ms, ev[2], ev[3]);
+        t_breed += b_ms;
+        t_roll += r_ms;
+        t_sel += s_ms;
         h->cur ^= 1;
         h->gen_host += 1;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     if (s != EMPC_OK) return s;
+    *breed_us = (float)(1000.0 * t_breed / reps);
     *rollout_us = (float)(1000.0 * t_roll / reps);
     *select_us = (float)(1000.0 * t_sel / reps);
     return EMPC_OK;

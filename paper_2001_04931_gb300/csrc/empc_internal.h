@@ -96,10 +96,15 @@ struct GradArgs {
 cudaError_t launch_grad(const GradArgs& a, int nx, int cands, int wpc, cudaStream_t st);
 size_t grad_smem_bytes(int nx, int nrg, int cands, int wpc, int n, int m, int p, int T, int ce);
 
+// Fused crossover + mutation (warm) or cold-start draw of candidates
+// cand_begin .. P-1 into pop_out (breed.cu).
+cudaError_t launch_breed(const RolloutArgs& a, cudaStream_t st);
+
 // BF16 tensor-core rollout (rollout_bf16.cu): n <= 128, m <= 64.
-cudaError_t launch_rollout_bf16(const RolloutArgs& a, cudaStream_t st);
+cudaError_t launch_rollout_bf16(const RolloutArgs& a, int groups, cudaStream_t st);
 bool rollout_bf16_supported(int n, int m, int T);
 size_t rollout_bf16_smem_bytes(int T);
+int rollout_bf16_threads();
 
 // Rollout tile.  kind 0 (block): ceil(n/rows) threads per candidate group,
 // `groups` candidate groups per CTA, one block barrier per step.  kind 1

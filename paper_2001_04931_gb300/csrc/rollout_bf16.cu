@@ -3,25 +3,28 @@
 //
 // For a tile of 128 candidates the step x_{k+1} = x_k + D x_k + B_d u_k
 // (D = A_d - I, Eq. first_order_integration in delta form) is one
-// 128 x 128 x 192 contraction per step:
-//   Y[c][i] = sum_{k<128} x_c[k] D[i][k] + sum_{j<64} u_c[j] B_d[i][j],
+// 128 x 128 x 192 contraction per step, accumulated onto the state itself:
+//   X[c][i] += sum_{k<128} x_c[k] D[i][k] + sum_{j<64} u_c[j] B_d[i][j],
 // with A = [x_c | u_c] (candidates x K, BF16) and B = [D | B_d] (states x K,
-// BF16, constant), both K-major with the 128-byte swizzle in shared memory,
-// and Y in tensor memory (TMEM lane = candidate, column = state).  Two
-// threads own each candidate (its TMEM lane), one per half of the states,
-// whose FP32 master copy they keep in registers: each adds Y to its states,
-// accumulates their stage cost (x_{k+1}-g)' Q (x_{k+1}-g) in eight partial
-// sums, rounds the new states and half of the next input u_{k+1} (knots kept
-// in registers per segment) to BF16, and writes them into the next step's A
-// row.  A is double-buffered: the next input is written while the step's
-// MMAs run, and each step's product runs as two N = 64 halves, one per
-// thread group, so one group's epilogue overlaps the other half's MMAs.  The input cost sum_k u_k' R u_k is added in closed form from
-// the knots (Gram of the knot weights), in FP32.
+// BF16, constant), both K-major with the 128-byte swizzle in shared memory.
+// The FP32 state X lives in tensor memory for the whole horizon (TMEM lane =
+// candidate, column = state): the MMA adds the increment to it, so no thread
+// keeps or updates a master copy.  Each step runs as four N = 32 column
+// chunks of threads; the product is issued as NG MMA groups of N = 128 / NG
+// columns (NG = 1, 2 or 4, chosen by the autotuner), each committed to its
+// own mbarrier, and the 512 threads are (chunk, candidate) pairs.  A thread waits for its chunk, reads its 32 states of
+// x_{k+1}, accumulates their stage cost (x_{k+1}-g)' Q (x_{k+1}-g), rounds
+// them to BF16 into the next step's A row, and writes its 16 inputs of
+// u_{k+1} (knots kept in registers per segment).  A is double-buffered, so
+// the early chunks' epilogues overlap the later chunks' MMAs.  The input cost
+// sum_k u_k' R u_k is added in closed form from the knots (Gram of the knot
+// weights), in FP32.
 //
 // Precision: D, B_d, x and u enter the product as BF16 (relative rounding
-// 2^-9); accumulation, the state update and the cost stay FP32.  Every
+// 2^-9); the accumulation onto the state and the cost stay FP32.  Every
 // mbarrier wait is bounded: past the limit the kernel sets status bit 2,
-// leaves the step loop, frees its tensor memory and returns.
+// leaves the step loop, waits (bounded) for its MMAs in flight, frees its
+// tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -36,10 +39,13 @@ constexpr int kKu = 64;          // K columns for the input (m padded)
 constexpr int kK = kKx + kKu;    // 192
 constexpr int kAtomBytes = 128 * 128;  // one 64-column swizzle atom of 128 rows
 constexpr int kOperandBytes = 3 * kAtomBytes;  // 128 rows x 192 BF16
-constexpr uint32_t kTmemCols = 128;    // the accumulator
+constexpr uint32_t kTmemCols = 128;    // the state (accumulator)
 constexpr long long kWaitPolls = 1ll << 26;
-constexpr int kThreads = 2 * kTileCands;  // two thread groups of 128 (4 warps each)
-constexpr int kKuHalf = kKu / 2;          // inputs per thread
+constexpr int kChunks = 4;                     // state column chunks, one MMA group each
+constexpr int kCW = kKx / kChunks;             // 32 states per chunk
+constexpr int kUW = kKu / kChunks;             // 16 inputs per chunk
+constexpr int kThreads = kChunks * kTileCands; // thread = (chunk, candidate row)
+static_assert(kCW == 32, "one 32x32b.x32 TMEM access per thread and step");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -111,21 +117,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Paired FP32 add and multiply (add/mul.rn.f32x2, sm_100 and later).
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
+__device__ __forceinline__ void tmem_st32(uint32_t addr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(
+            addr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+        "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+        "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+        "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+        "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+        "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+        "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+        "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+        "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+        : "memory");
 }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
+
+// Paired FP32 add and multiply (round to nearest, sm_100 and later).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -150,11 +163,16 @@ struct Bf16Layout {
     static constexpr int kQ = kG + 128 * 4;            // diag Q [128] f32
     static constexpr int kKnots = kQ + 128 * 4;        // KnotStep[T]
     __host__ __device__ static int par(int T) { return kKnots + 16 * T; }  // int[2*128]
-    __host__ __device__ static int part(int T) { return par(T) + 8 * kTileCands; }  // f32[128]
-    __host__ __device__ static int total(int T) { return part(T) + 4 * kTileCands + 1024; }
+    __host__ __device__ static int part(int T) { return par(T) + 8 * kTileCands; }  // f32[4][128]
+    __host__ __device__ static int total(int T) {
+        return part(T) + 4 * kChunks * kTileCands + 1024;
+    }
 };
 
+template <int NG>
 __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const RolloutArgs a) {
+    static_assert(NG == 1 || NG == 2 || NG == 4, "MMA groups");
+    constexpr int kGW = kKx / NG;  // columns (states) per MMA group
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t* sA[2] = {sm + Bf16Layout::kA0, sm + Bf16Layout::kA1};
@@ -164,12 +182,12 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
     KnotStep* ks = reinterpret_cast<KnotStep*>(sm + Bf16Layout::kKnots);
     int* par = reinterpret_cast<int*>(sm + Bf16Layout::par(a.T));
     float* spart = reinterpret_cast<float*>(sm + Bf16Layout::part(a.T));
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[kChunks];
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int grp = warp >> 2;                     // state half / input half of this thread
+    const int q = warp >> 2;                         // state chunk / input chunk of this thread
     const int row = ((warp & 3) << 5) | (tid & 31);  // candidate row = TMEM lane
     const int n = a.n, m = a.m, p = a.p, T = a.T;
     const int c0 = a.cand_begin + blockIdx.x * kTileCands;
@@ -177,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
     pdl_launch_dependents();
 
     // ---- constant operand B = [D | B_d] (rows = states), goal, Q, knot table
-    for (int idx = tid; idx < 128 * (kK / 8); idx += blockDim.x) {  // (all threads)
+    for (int idx = tid; idx < 128 * (kK / 8); idx += blockDim.x) {
         const int i = idx / (kK / 8), k0 = (idx % (kK / 8)) * 8;
         float v[8];
 #pragma unroll
@@ -204,31 +222,47 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[g])));
         abort_sh = 0;
     }
 
     // ---- knots: bred (to pop_out) or given (pop_in)
     pdl_wait_primary();
     const uint32_t gen = a.gen ? *a.gen : 0u;
-    if (a.mode == kWarm && grp == 0) {
+    if (a.mode == kWarm && tid < kTileCands) {
         int s1, s2;
-        parents_of<false>(a, cand, gen, s1, s2);
-        par[2 * row] = s1;
-        par[2 * row + 1] = s2;
+        parents_of<false>(a, c0 + tid, gen, s1, s2);
+        par[2 * tid] = s1;
+        par[2 * tid + 1] = s2;
     }
     __syncthreads();
     const int D = m * p;
-    if (a.mode != kEval) {
+    if (a.mode == kWarm) {
+        const int nhex = (D + 15) >> 4;
+        for (int it = tid; it < nhex * kTileCands; it += blockDim.x) {
+            const int t = it % kTileCands, hex = it / kTileCands;
+            const int c = c0 + t;
+            if (c >= a.P) continue;
+            const int s1 = par[2 * t], s2 = par[2 * t + 1];
+            auto emit = [&](int qq, float v) { a.pop_out[(size_t)qq * a.P + c] = v; };
+            if (s2 < 0) {
+                for (int w = 0; w < 16; ++w)
+                    if (hex * 16 + w < D)
+                        emit(hex * 16 + w, __ldcg(a.pop_in + (size_t)(hex * 16 + w) * a.P + s1));
+            } else {
+                breed_hex_warm<false>(a, c, hex, gen, s1, s2, emit);
+            }
+        }
+    } else if (a.mode == kCold) {
         const int nquad = (D + 3) >> 2;
         for (int it = tid; it < nquad * kTileCands; it += blockDim.x) {
             const int t = it % kTileCands, quad = it / kTileCands;
             const int c = c0 + t;
             if (c >= a.P) continue;
             float v[4];
-            breed_quad<false>(a, c, quad, gen, a.mode == kWarm ? par[2 * t] : 0,
-                              a.mode == kWarm ? par[2 * t + 1] : -1, v);
+            breed_quad<false>(a, c, quad, gen, 0, -1, v);
 #pragma unroll
             for (int w = 0; w < 4; ++w)
                 if (quad * 4 + w < D) a.pop_out[(size_t)(quad * 4 + w) * a.P + c] = v[w];
@@ -242,26 +276,31 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
     const float* src = a.mode == kEval ? a.pop_in : a.pop_out;
     const bool live = cand < a.P;
 
-    // ---- initial state: FP32 master of own half in registers, BF16 copy in A[0]
-    float xs[64];
+    // ---- initial state: FP32 into this thread's chunk of its TMEM lane, BF16 into A[0]
+    {
+        float x0[kCW];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
-        const int i = grp * 64 + j;
-        xs[j] = i < n ? a.x0[i] : 0.0f;
+        for (int j = 0; j < kCW; ++j) {
+            const int i = q * kCW + j;
+            x0[j] = i < n ? a.x0[i] : 0.0f;
+        }
+        tmem_st32(lane_base + q * kCW, x0);
+#pragma unroll
+        for (int j = 0; j < kCW; j += 8) put8(sA[0], row, q * kCW + j, x0 + j);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-#pragma unroll
-    for (int j = 0; j < 64; j += 8) put8(sA[0], row, grp * 64 + j, xs + j);
-    // knots of the current segment (own half of the inputs)
-    float ua[kKuHalf], ub[kKuHalf];
-    const int i0 = grp * kKuHalf;
+    // knots of the current segment (this thread's chunk of the inputs)
+    float ua[kUW], ub[kUW];
+    const int i0 = q * kUW;
     int seg = -1;
     float Ju = 0.0f;  // input cost of own inputs, closed form, accumulated per segment
     auto load_segment = [&](int s) {
 #pragma unroll
-        for (int j = 0; j < kKuHalf; ++j) {
+        for (int j = 0; j < kUW; ++j) {
             const int i = i0 + j;
-            ua[j] = (live && i < m) ? src[(size_t)(i * p + s) * a.P + cand] : 0.0f;
-            ub[j] = (live && i < m && s + 1 < p) ? src[(size_t)(i * p + s + 1) * a.P + cand] : 0.0f;
+            ua[j] = (live && i < m) ? __ldcg(src + (size_t)(i * p + s) * a.P + cand) : 0.0f;
+            ub[j] = (live && i < m && s + 1 < p) ? __ldcg(src + (size_t)(i * p + s + 1) * a.P + cand)
+                                                  : 0.0f;
         }
         // segments come in order, each once: W_ss U_s^2 + 2 W_s,s+1 U_s U_s+1,
         // plus W_{p-1,p-1} U_{p-1}^2 with the last segment
@@ -269,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         const float wo = s + 1 < p ? 2.0f * a.gram[p + s] : 0.0f;
         const float wl = s + 2 == p ? a.gram[s + 1] : 0.0f;
 #pragma unroll
-        for (int j = 0; j < kKuHalf; ++j) {
+        for (int j = 0; j < kUW; ++j) {
             if (i0 + j < m) {
                 float t = wd * ua[j] * ua[j];
                 t = fmaf(wo * ua[j], ub[j], t);
@@ -284,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
             load_segment(seg);
         }
 #pragma unroll
-        for (int j = 0; j < kKuHalf; j += 8) {
+        for (int j = 0; j < kUW; j += 8) {
             float v[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = fmaf(st.w1, ub[j + e], st.w0 * ua[j + e]);
@@ -296,7 +335,11 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
     float2 jacc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
                       make_float2(0.f, 0.f)};
     bool ok = true;
-    const uint32_t idesc = idesc_bf16(64);
+    int issued = -1;  // last step whose MMAs thread 0 committed
+    const uint32_t idesc = idesc_bf16(kGW);
+    const int grp = q * NG / kChunks;  // the MMA group holding this thread's chunk
+    const float4* g4 = reinterpret_cast<const float4*>(sg + q * kCW);
+    const float4* q4 = reinterpret_cast<const float4*>(sq + q * kCW);
     for (int k = 0; k < T; ++k) {
         uint8_t* Acur = sA[k & 1];
         uint8_t* Anext = sA[(k + 1) & 1];
@@ -305,67 +348,68 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         if (!__syncthreads_and(ok)) break;  // every thread leaves together
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // descriptors advance by (byte offset >> 4) in their start-address field
+            // descriptors advance by (byte offset >> 4) in their start-address field;
+            // group g uses rows g*kGW .. of B (rows of 128 B within each atom)
             const uint64_t ad0 = sdesc(smem_u32(Acur)), bd0 = sdesc(smem_u32(sB));
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int g = 0; g < NG; ++g) {
 #pragma unroll
                 for (int kk = 0; kk < kK / 16; ++kk) {
                     const uint32_t off = ((kk >> 2) * kAtomBytes + (kk & 3) * 32) >> 4;
-                    mma_bf16(tmem + h * 64, ad0 + off, bd0 + off + ((h * 64 * 128) >> 4), idesc,
-                             kk > 0 ? 1u : 0u);
+                    mma_bf16(tmem + g * kGW, ad0 + off, bd0 + off + ((g * kGW * 128) >> 4), idesc,
+                             1u);
                 }
-                mma_commit(&mbar[h]);
+                mma_commit(&mbar[g]);
             }
+            issued = k;
         }
-        // off the critical path: the next input, while the MMAs run (Anext was
-        // last read by the previous step's MMAs, which have completed)
+        // off the critical path: this thread's inputs of u_{k+1}, while the MMAs
+        // run (Anext was last read by the previous step's MMAs, which have completed)
         if (k + 1 < T) write_input(Anext, ks[k + 1]);
-        // epilogue of this thread's half of the states
         if (!mbar_wait(&mbar[grp], (uint32_t)(k & 1))) {
             ok = false;
             continue;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float y[2][32];
-        tmem_ld32(lane_base + (2 * grp) * 32, y[0]);
-        tmem_ld32(lane_base + (2 * grp + 1) * 32, y[1]);
+        float x[kCW];
+        tmem_ld32(lane_base + q * kCW, x);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c2 = 0; c2 < 2; ++c2) {
-            const int ch = 2 * grp + c2;
-            const float4* g4 = reinterpret_cast<const float4*>(sg + ch * 32);
-            const float4* q4 = reinterpret_cast<const float4*>(sq + ch * 32);
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                const int jj = c2 * 32 + j;
-                const float4 gg = g4[j / 4], qq = q4[j / 4];
-                const float2 x01 = add2(make_float2(xs[jj], xs[jj + 1]),
-                                        make_float2(y[c2][j], y[c2][j + 1]));
-                const float2 x23 = add2(make_float2(xs[jj + 2], xs[jj + 3]),
-                                        make_float2(y[c2][j + 2], y[c2][j + 3]));
-                xs[jj] = x01.x; xs[jj + 1] = x01.y; xs[jj + 2] = x23.x; xs[jj + 3] = x23.y;
-                const float2 e01 = add2(x01, make_float2(-gg.x, -gg.y));
-                const float2 e23 = add2(x23, make_float2(-gg.z, -gg.w));
-                jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[(j / 4) & 3]);
-                jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[(j / 4) & 3]);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; j += 8) put8(Anext, row, ch * 32 + j, xs + c2 * 32 + j);
+        for (int j = 0; j < kCW; j += 4) {
+            const float4 gg = g4[j / 4], qq = q4[j / 4];
+            const float2 e01 = add2(make_float2(x[j], x[j + 1]), make_float2(-gg.x, -gg.y));
+            const float2 e23 = add2(make_float2(x[j + 2], x[j + 3]), make_float2(-gg.z, -gg.w));
+            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[(j / 4) & 3]);
+            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[(j / 4) & 3]);
         }
+        if (k + 1 < T) {
+#pragma unroll
+            for (int j = 0; j < kCW; j += 8) put8(Anext, row, q * kCW + j, x + j);
+        }
+    }
+    // an abandoned step may still have MMAs in flight: wait (bounded) for them
+    // before the tensor memory is freed
+    if (tid == 0 && issued >= 0) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+            if (!mbar_wait(&mbar[g], (uint32_t)(issued & 1))) ok = false;
     }
     if (!ok) abort_sh = 1;
     float jown = Ju;
 #pragma unroll
     for (int j = 0; j < 4; ++j) jown += jacc[j].x + jacc[j].y;
-    if (grp == 1) spart[row] = jown;
+    spart[q * kTileCands + row] = jown;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (abort_sh) {
         if (tid == 0 && a.status) atomicOr(a.status, 2);
-    } else if (live && grp == 0) {
-        a.cost[cand] = finite_or_inf(jown + spart[row]);
+    } else if (live && q == 0) {
+        float J = spart[row];
+#pragma unroll
+        for (int c = 1; c < kChunks; ++c) J += spart[c * kTileCands + row];
+        a.cost[cand] = finite_or_inf(J);
     }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
@@ -375,24 +419,36 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
 
 size_t rollout_bf16_smem_bytes(int T) { return (size_t)Bf16Layout::total(T); }
 
+int rollout_bf16_threads() { return kThreads; }
+
 bool rollout_bf16_supported(int n, int m, int T) {
     return n <= kKx && m <= kKu && rollout_bf16_smem_bytes(T) <= 227u * 1024u;
 }
 
-cudaError_t launch_rollout_bf16(const RolloutArgs& a, cudaStream_t st) {
-    if (!rollout_bf16_supported(a.n, a.m, a.T)) return cudaErrorInvalidConfiguration;
+template <int NG>
+cudaError_t launch_groups(const RolloutArgs& a, cudaStream_t st) {
     const size_t smem = rollout_bf16_smem_bytes(a.T);
     static int smem_cap = 48 * 1024;
     if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_bf16_kernel,
+        cudaError_t e = cudaFuncSetAttribute(rollout_bf16_kernel<NG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         smem_cap = (int)smem;
     }
     const int grid = (a.P - a.cand_begin + kTileCands - 1) / kTileCands;
     if (grid <= 0) return cudaSuccess;
-    return launch_kernel(rollout_bf16_kernel, dim3(grid), dim3(kThreads), smem, st,
+    return launch_kernel(rollout_bf16_kernel<NG>, dim3(grid), dim3(kThreads), smem, st,
                          a.pdl != 0, a);
+}
+
+cudaError_t launch_rollout_bf16(const RolloutArgs& a, int groups, cudaStream_t st) {
+    if (!rollout_bf16_supported(a.n, a.m, a.T)) return cudaErrorInvalidConfiguration;
+    switch (groups) {
+        case 1: return launch_groups<1>(a, st);
+        case 2: return launch_groups<2>(a, st);
+        case 4: return launch_groups<4>(a, st);
+        default: return cudaErrorInvalidConfiguration;
+    }
 }
 
 }  // namespace empc

@@ -172,7 +172,7 @@ int rollout_shapes(int n, TileShape* out, int cap) {
 }
 
 int rollout_threads(const TileShape& s, int n) {
-    if (s.kind == 2) return 128;
+    if (s.kind == 2) return rollout_bf16_threads();
     if (s.kind == 1) return 32 * s.groups;
     return ((n + s.rows - 1) / s.rows) * s.groups;
 }
@@ -192,11 +192,10 @@ size_t rollout_smem_bytes(const TileShape& s, int n, int m, int p, int T) {
         const int cpw = (32 / nrg) * s.cands;
         const int xsw = round_up(cpw, 4);
         const int per_warp = round_up(2 * xr * xsw + m * p * xsw + 2 * xsw, 4);
-        const int head = round_up(m * xr, 4) + 4 * T;
+        const int head = round_up(m * xr, 4) + 4 * T + round_up(n * (s.nx + 2), 4);
         return sizeof(float) * (size_t)(head + s.groups * per_warp);
     }
     const BlockLayout L(s.nx, s.groups * s.cands, m, p, T);
-    (void)n;
     return sizeof(float) * (size_t)L.total;
 }
 
@@ -210,7 +209,7 @@ bool rollout_shape_supported(const TileShape& s, int n, int m, int p, int T) {
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, const TileShape& s, cudaStream_t st) {
-    if (s.kind == 2) return launch_rollout_bf16(a, st);
+    if (s.kind == 2) return launch_rollout_bf16(a, s.groups, st);
     if (s.nx != compiled_nx(a.n)) return cudaErrorInvalidConfiguration;
     return s.kind == 1 ? launch_rollout_warp(a, s, st) : launch_rollout_block(a, s, st);
 }

@@ -74,17 +74,10 @@ __device__ __forceinline__ void knot_force(const float* BTs, int ldb, const floa
     }
 }
 
-// Paired FP32 fused multiply-add (fma.rn.f32x2, sm_100 and later): two
-// independent IEEE round-to-nearest FMAs in one instruction.
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
+// Paired FP32 fused multiply-add (sm_100 and later): two independent IEEE
+// round-to-nearest FMAs in one instruction, through the CUDA intrinsic so the
+// compiler keeps the operands in register pairs.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // Pair-interleaved state tile: row k of column col lives at
 // ((k / 2) * xs + col) * 2 + (k & 1), so one vector load returns rows
@@ -156,13 +149,14 @@ __device__ __forceinline__ void state_product(const float (&d)[R][NX], const flo
         for (int c = 0; c < C; ++c) acc[r][c] += odd[r][c];
 }
 
-// Population loads: through the read-only path when the population cannot
-// change during the kernel, else through L2 (other CTAs of a persistent
-// kernel write it).
+// Population loads.  The population is written by the kernel launched just
+// before (or by other CTAs of a persistent kernel), which may still be running
+// when this one starts (programmatic dependent launch): every read goes
+// through L2 with a coherent load, never the read-only path, whose contents
+// the compiler may assume fixed for the whole kernel.
 template <bool COHERENT>
 __device__ __forceinline__ float pop_load(const float* p) {
-    if constexpr (COHERENT) return __ldcg(p);
-    else return __ldg(p);
+    return __ldcg(p);
 }
 
 // Parents of child c as population columns (s1, s2); s2 < 0 marks an elite
@@ -199,13 +193,17 @@ __device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad
             if (q0 + w < D) v[w] = pop_load<COHERENT>(a.pop_in + (size_t)(q0 + w) * a.P + c);
     } else if (a.mode == kCold) {
         const Words4 o = draw(a.seed, (uint32_t)c, gen, kDrawInit, (uint32_t)quad);
+        int i = q0 / a.p, j = q0 - i * a.p;  // input and knot of q0, advanced below
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int q = q0 + w;
             if (q < D) {
-                const int i = q / a.p;
                 const float lo = a.umin[i], hi = a.umax[i];
                 v[w] = clamp_to(__fmaf_rn(__fsub_rn(hi, lo), unit_closed_open(o.w[w]), lo), lo, hi);
+            }
+            if (++j == a.p) {
+                j = 0;
+                ++i;
             }
         }
     } else if (s2 < 0) {
@@ -229,6 +227,69 @@ __device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad
         uint32_t gate_blk = 0xFFFFFFFFu;
         float z[4];
         bool have_z = false;
+        int i = q0 / a.p, j = q0 - i * a.p;  // input and knot of q0, advanced below
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int q = q0 + w;
+            if (q < D) {
+                bool mut = true;
+                if (a.gate != 2) {
+                    const uint32_t gb = (a.gate == 0) ? (uint32_t)i : (uint32_t)q;
+                    if ((gb >> 4) != gate_blk) {
+                        gate_blk = gb >> 4;
+                        gw = draw(a.seed, (uint32_t)c, gen, kDrawGate, gate_blk);
+                    }
+                    mut = ((gw.w[(gb >> 2) & 3u] >> (8u * (gb & 3u))) & 0xFFu) <
+                          (uint32_t)a.pm256;
+                }
+                float val = mate[w];
+                if (mut) {
+                    if (!have_z) {
+                        const Words4 nz =
+                            draw(a.seed, (uint32_t)c, gen, kDrawNoise, (uint32_t)quad);
+                        gauss_pair(nz.w[0], nz.w[1], &z[0], &z[1]);
+                        gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
+                        have_z = true;
+                    }
+                    val = __fmaf_rn(a.sigma, z[w], mate[w]);
+                }
+                v[w] = clamp_to(val, a.umin[i], a.umax[i]);
+            }
+            if (++j == a.p) {
+                j = 0;
+                ++i;
+            }
+        }
+    }
+}
+
+// Knots q0 .. q0+15 (q0 = 16 hex) of warm child c >= E, mated from parent
+// columns s1, s2 and mutated: the same draws and arithmetic as four
+// breed_quad calls, with each Philox block computed once (one crossover
+// block covers 16 knots, one gate block 16 gate bytes).  Knots are produced
+// a quad at a time and handed to emit(q, value).
+template <bool COHERENT, class Emit>
+__device__ __forceinline__ void breed_hex_warm(const RolloutArgs& a, int c, int hex,
+                                               uint32_t gen, int s1, int s2, Emit&& emit) {
+    const int D = a.m * a.p;
+    const Words4 cr = draw(a.seed, (uint32_t)c, gen, kDrawCross, (uint32_t)hex);
+    Words4 gw;
+    uint32_t gate_blk = 0xFFFFFFFFu;
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) {
+        const int q0 = hex * 16 + qd * 4;
+        if (q0 >= D) break;
+        float mate[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int q = q0 + w;
+            const uint32_t cb = (cr.w[qd] >> (8 * w)) & 0xFFu;
+            mate[w] = q < D ? pop_load<COHERENT>(a.pop_in + (size_t)q * a.P +
+                                                 (cb < (uint32_t)a.pc256 ? s2 : s1))
+                            : 0.0f;
+        }
+        float z[4];
+        bool have_z = false;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int q = q0 + w;
@@ -246,14 +307,15 @@ __device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad
             float val = mate[w];
             if (mut) {
                 if (!have_z) {
-                    const Words4 nz = draw(a.seed, (uint32_t)c, gen, kDrawNoise, (uint32_t)quad);
+                    const Words4 nz =
+                        draw(a.seed, (uint32_t)c, gen, kDrawNoise, (uint32_t)(q0 >> 2));
                     gauss_pair(nz.w[0], nz.w[1], &z[0], &z[1]);
                     gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
                     have_z = true;
                 }
                 val = __fmaf_rn(a.sigma, z[w], mate[w]);
             }
-            v[w] = clamp_to(val, a.umin[i], a.umax[i]);
+            emit(q, clamp_to(val, a.umin[i], a.umax[i]));
         }
     }
 }
@@ -276,20 +338,42 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
         }
         if (WARP) __syncwarp(); else __syncthreads();
     }
-    for (int it = tid; it < nquad * count; it += nthr) {
-        const int t = it % count;
-        const int quad = it / count;
-        const int c = c0 + t;
-        float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (c < a.P)
-            breed_quad<COHERENT>(a, c, quad, gen, a.mode == kWarm ? par[2 * t] : 0,
-                                 a.mode == kWarm ? par[2 * t + 1] : -1, v);
+    if (a.mode == kWarm) {
+        // children in 16-knot items (shared draws), elites copied
+        const int nhex = (D + 15) >> 4;
+        for (int it = tid; it < nhex * count; it += nthr) {
+            const int t = it % count;
+            const int hex = it / count;
+            const int c = c0 + t;
+            const int s1 = par[2 * t], s2 = par[2 * t + 1];
+            auto emit = [&](int q, float v) {
+                if (Us) Us[q * xs + t] = v;
+                if (c < a.P) a.pop_out[(size_t)q * a.P + c] = v;
+            };
+            if (c >= a.P || s2 < 0) {
+                for (int w = 0; w < 16; ++w) {
+                    const int q = hex * 16 + w;
+                    if (q < D) emit(q, c < a.P ? pop_load<COHERENT>(a.pop_in + (size_t)q * a.P + s1)
+                                               : 0.0f);
+                }
+            } else {
+                breed_hex_warm<COHERENT>(a, c, hex, gen, s1, s2, emit);
+            }
+        }
+    } else {
+        for (int it = tid; it < nquad * count; it += nthr) {
+            const int t = it % count;
+            const int quad = it / count;
+            const int c = c0 + t;
+            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (c < a.P) breed_quad<COHERENT>(a, c, quad, gen, 0, -1, v);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int q = quad * 4 + w;
-            if (q < D) {
-                if (Us) Us[q * xs + t] = v[w];
-                if (a.mode != kEval && c < a.P) a.pop_out[(size_t)q * a.P + c] = v[w];
+            for (int w = 0; w < 4; ++w) {
+                const int q = quad * 4 + w;
+                if (q < D) {
+                    if (Us) Us[q * xs + t] = v[w];
+                    if (a.mode != kEval && c < a.P) a.pop_out[(size_t)q * a.P + c] = v[w];
+                }
             }
         }
     }

@@ -33,9 +33,11 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
     extern __shared__ __align__(16) float smem[];
     const int m = a.m, T = a.T;
     const int warp = threadIdx.x >> 5;
+    constexpr int DS = NX + 2;  // D row stride: 8-byte pairs, rows spread over the banks
     float* BTs = smem;
     KnotStep* ks = reinterpret_cast<KnotStep*>(smem + round_up(m * XR, 4));
-    float* W = smem + round_up(m * XR, 4) + 4 * T + warp * warp_slice_floats<NX, C>(m * a.p);
+    float* Ds = smem + round_up(m * XR, 4) + 4 * T;
+    float* W = Ds + round_up(a.n * DS, 4) + warp * warp_slice_floats<NX, C>(m * a.p);
     const int c0 = a.cand_begin + (blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
     pdl_launch_dependents();
     for (int i = threadIdx.x; i < m * XR; i += blockDim.x) {
@@ -43,9 +45,13 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
         BTs[i] = row < a.n ? a.BT[col * a.n + row] : 0.0f;
     }
     for (int k = threadIdx.x; k < T; k += blockDim.x) ks[k] = a.ktab[k];
+    for (int i = threadIdx.x; i < a.n * DS; i += blockDim.x) {
+        const int r = i / DS, k = i % DS;
+        Ds[i] = k < a.n ? a.D[r * a.n + k] : 0.0f;
+    }
     __syncthreads();
     if (c0 >= a.P) return;  // no block barrier follows
-    warp_tile<NX, C>(a, c0, W, BTs, ks);
+    warp_tile<NX, C>(a, c0, W, BTs, ks, Ds, DS);
 }
 
 template <int NX, int C>

@@ -106,12 +106,15 @@ __host__ __device__ constexpr int warp_slice_floats(int D) {
 
 // One warp breeds (or loads) and rolls out candidates c0 .. c0+CPW-1 of
 // problem `a` and writes their costs.  W is the warp's shared-memory slice;
-// BTs ([m][XR], rows past n zero) and ks (knot table) are staged by the CTA.
+// BTs ([m][XR], rows past n zero) and ks (knot table) are staged by the CTA,
+// and so is D when Ds is given ([n][ds] with ds >= NX, columns past n zero;
+// otherwise the rows are read from global memory).
 // Reads the population, the elites and the generation counter only after
 // pdl_wait_primary(); COHERENT reads them through L2 (persistent kernels).
 template <int NX, int C, bool COHERENT = false>
 __device__ __forceinline__ void warp_tile(const RolloutArgs& a, int c0, float* W,
-                                          const float* BTs, const KnotStep* ks) {
+                                          const float* BTs, const KnotStep* ks,
+                                          const float* Ds = nullptr, int ds = 0) {
     constexpr int NRG = nrg_of(NX);
     constexpr int R = (NX + NRG - 1) / NRG;
     constexpr int XR = NRG * R;
@@ -137,11 +140,18 @@ __device__ __forceinline__ void warp_tile(const RolloutArgs& a, int c0, float* W
     for (int r = 0; r < R; ++r) {
         const int row = rg * R + r;
         const bool ok = row < a.n;
+        if (Ds) {
 #pragma unroll
-        for (int kp = 0; kp < KP; ++kp) {
-            const int k = 2 * kp;
-            d2[r][kp] = make_float2((ok && k < a.n) ? a.D[row * a.n + k] : 0.0f,
-                                    (ok && k + 1 < a.n) ? a.D[row * a.n + k + 1] : 0.0f);
+            for (int kp = 0; kp < KP; ++kp)
+                d2[r][kp] = ok ? *reinterpret_cast<const float2*>(Ds + row * ds + 2 * kp)
+                               : make_float2(0.0f, 0.0f);
+        } else {
+#pragma unroll
+            for (int kp = 0; kp < KP; ++kp) {
+                const int k = 2 * kp;
+                d2[r][kp] = make_float2((ok && k < a.n) ? a.D[row * a.n + k] : 0.0f,
+                                        (ok && k + 1 < a.n) ? a.D[row * a.n + k + 1] : 0.0f);
+            }
         }
         qd[r] = ok ? a.qdiag[row] : 0.0f;
         gl[r] = ok ? a.goal[row] : 0.0f;

@@ -1,22 +1,24 @@
 // Elite selection: the E lowest-cost candidates in (cost, index) order.
 //
 // Algorithm 1's parent line keeps the numParents U arrays with the lowest
-// costs (Sec. V, parent selection).  One CTA of 1024 threads per problem:
-//   1. map each FP32 cost to an order-preserving 32-bit key (NaN as +inf);
-//   2. radix-select the E-th smallest key, 8 bits per pass, with a shared
-//      histogram and a warp scan of its 256 bins;
-//   3. one block-wide exclusive scan of (less-than, equal) counts in index
-//      order compacts the keys below the threshold plus the lowest-index
-//      keys equal to it: exactly E distinct (key, index) pairs;
-//   4. rank each selected pair by counting the pairs below it (E^2 shared
-//      compares, E <= 2048) and scatter to rank order;
-//   5. copy the best candidate's knots and cost out and bump the generation
-//      counter that keys the next generation's draws.
-// Fast path (steps 2-3 replaced): slots 0..E-1 always hold E candidates
-// (after a warm start, the previous elites re-evaluated), so the E-th
-// smallest (key, index) pair is at most K*, the largest pair among those
-// slots.  When few candidates lie at or below K* they are compacted
-// directly and ranked by counting; otherwise the radix select runs.
+// costs (Sec. V, parent selection).  One CTA of 512 threads per problem.
+// Each cost maps to an order-preserving 32-bit key (NaN as +inf), paired
+// with its index into a unique 64-bit (key, index) word.  The kernel picks a
+// threshold key tau with at least E and at most 2048 words whose keys are at
+// most tau, compacts those words into shared memory and ranks them: by
+// counting when there are at most 256, else by sorting 64-word chunks (one
+// warp each, register shuffles) and binary-searching the other chunks.
+// Thresholds tried, in order:
+//   1. the words of sixteen of the slots 0..E-1 (after a warm start those
+//      slots hold the previous elites in rank order, so one of them usually
+//      bounds a little more than E words), and K*, the largest word of those
+//      slots (which always bounds at least E);
+//   2. a quantile of a sorted stride sample of the words, a little above the
+//      expected E/P quantile;
+//   3. an exact radix select (8 bits per pass, warp-aggregated shared
+//      histogram) of the E-th smallest word.
+// Then the best candidate's knots and cost are copied out and the generation
+// counter that keys the next generation's draws is bumped.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,7 +28,7 @@
 namespace empc {
 namespace {
 
-constexpr int kSelThreads = 1024;
+constexpr int kSelThreads = 512;
 constexpr int kMaxElite = 2048;
 
 __device__ __forceinline__ uint32_t order_key(float c) {
@@ -35,7 +37,7 @@ __device__ __forceinline__ uint32_t order_key(float c) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Exclusive block scan of one uint32 per thread (blockDim == 1024).
+// Exclusive block scan of one uint32 per thread (blockDim a multiple of 32, <= 1024).
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t incl = v;
@@ -47,7 +49,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     if (lane == 31) warp_tot[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = warp_tot[lane];
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -63,200 +65,334 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 }
 
 // Copy the best candidate's knots and cost out; bump the generation counter.
-__device__ __forceinline__ void finish_select(const float* __restrict__ cost, int P,
-                                              const float* __restrict__ pop, int D,
-                                              float* __restrict__ best_knots,
-                                              float* __restrict__ best_cost,
-                                              uint32_t* __restrict__ gen,
-                                              int* __restrict__ status, int best) {
-    for (int q = threadIdx.x; q < D; q += blockDim.x) best_knots[q] = pop[(size_t)q * P + best];
+__device__ __forceinline__ void finish_select(const float* cost, int P,
+                                              const float* pop, int D,
+                                              float* best_knots,
+                                              float* best_cost,
+                                              uint32_t* gen,
+                                              int* status, int best) {
+    for (int q = threadIdx.x; q < D; q += blockDim.x) best_knots[q] = __ldcg(pop + (size_t)q * P + best);
     if (threadIdx.x == 0) {
-        const float bc = cost[best];
+        const float bc = __ldcg(cost + best);
         *best_cost = bc;
         if (gen) *gen += 1u;
         if (status && !(bc < __int_as_float(0x7f800000))) atomicOr(status, 1);
     }
 }
 
+// One compare-exchange of a bitonic network, seen from the element at
+// position p holding `mine` whose partner p ^ j holds `other`.
+__device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long mine,
+                                                           unsigned long long other, int p,
+                                                           int j, int k) {
+    const bool lower = (p & j) == 0, up = (p & k) == 0;
+    return (lower == up) ? min(mine, other) : max(mine, other);
+}
+
+// Sort the 64 words s[0..64) within one warp (two per lane, bitonic network
+// over register shuffles), in place.
+__device__ __forceinline__ void warp_sort64(unsigned long long* s) {
+    const int lane = (int)(threadIdx.x & 31u);
+    const int p0 = 2 * lane;
+    unsigned long long v0 = s[p0], v1 = s[p0 + 1];
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 1) {
+                const unsigned long long lo = min(v0, v1), hi = max(v0, v1);
+                const bool up = (p0 & k) == 0;
+                v0 = up ? lo : hi;
+                v1 = up ? hi : lo;
+            } else {
+                const unsigned long long o0 = __shfl_xor_sync(0xffffffffu, v0, j >> 1);
+                const unsigned long long o1 = __shfl_xor_sync(0xffffffffu, v1, j >> 1);
+                v0 = bitonic_keep(v0, o0, p0, j, k);
+                v1 = bitonic_keep(v1, o1, p0 + 1, j, k);
+            }
+        }
+    }
+    __syncwarp();
+    s[p0] = v0;
+    s[p0 + 1] = v1;
+    __syncwarp();
+}
+
+// Rank the L distinct words s[0..L) (L <= kMaxElite): sort them in chunks
+// of 64 (one warp per chunk), then rank each word as its place in its own
+// chunk plus, for every other chunk, the number of smaller words there
+// (binary search).  visit(rank, word) is called once per word, by the thread
+// that ranked it.  Pads s up to a multiple of 64; every thread of the block
+// must call it; the caller synchronizes after it.
+template <class Visit>
+__device__ __forceinline__ void rank_words(unsigned long long* s, int L, Visit&& visit) {
+    const int Lp = (L + 63) & ~63;
+    for (int i = L + (int)threadIdx.x; i < Lp; i += blockDim.x) s[i] = ~0ull;
+    __syncthreads();
+    const int C = Lp >> 6;
+    for (int c = (int)(threadIdx.x >> 5); c < C; c += (int)(blockDim.x >> 5)) warp_sort64(s + 64 * c);
+    __syncthreads();
+    for (int e = (int)threadIdx.x; e < L; e += blockDim.x) {
+        const unsigned long long x = s[e];
+        const int ce = e >> 6;
+        int rank = e & 63;
+        for (int c = 0; c < C; ++c) {
+            if (c == ce) continue;
+            const unsigned long long* ch = s + 64 * c;
+            int pos = 0;
+#pragma unroll
+            for (int step = 32; step > 0; step >>= 1)
+                if (ch[pos + step - 1] < x) pos += step;
+            if (pos == 63 && ch[63] < x) pos = 64;
+            rank += pos;
+        }
+        visit(rank, x);
+    }
+}
+
+// Number of words whose key is at most ktau, block-wide (every thread gets it).
 template <int KPT>
-__global__ void __launch_bounds__(kSelThreads) select_kernel(
-    const float* __restrict__ cost, int P, int E, const float* __restrict__ pop, int D,
-    int* __restrict__ elite_idx, float* __restrict__ elite_cost, float* __restrict__ best_knots,
-    float* __restrict__ best_cost, uint32_t* __restrict__ gen, int* __restrict__ status) {
+__device__ __forceinline__ uint32_t count_at_most(const unsigned long long (&w)[KPT],
+                                                  uint32_t ktau, uint32_t* warp_tot) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) c += (uint32_t)(w[j] >> 32) <= ktau;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = c;
+    __syncthreads();
+    uint32_t L = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) L += warp_tot[w2];
+    return L;
+}
+
+template <int KPT>
+__global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
+    const float* cost, int P, int E, const float* pop, int D,
+    int* elite_idx, float* elite_cost, float* best_knots,
+    float* best_cost, uint32_t* gen, int* status) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t s_digit, s_rem;
-    __shared__ int s_best;
     __shared__ uint32_t s_count;
-    __shared__ unsigned long long s_kstar;
     __shared__ unsigned long long s_red64[32];
     __shared__ unsigned long long sel[kMaxElite];
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // the costs come from the kernel this one may overlap: every read of them
+    // below is a coherent (L2) load issued after the wait
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    uint32_t key[KPT];
+    constexpr unsigned long long kNone = ~0ull;
+    unsigned long long w[KPT];  // (key, index); kNone past P
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         const int idx = tid * KPT + j;
-        key[j] = idx < P ? order_key(cost[idx]) : 0xFFFFFFFFu;
+        w[j] = idx < P ? (((unsigned long long)order_key(__ldcg(cost + idx)) << 32) | (uint32_t)idx)
+                       : kNone;
     }
 
-    // ---- fast path: bound from slots 0..E-1
-    const int lane = tid & 31, warp = tid >> 5;
+    // ---- 1. thresholds from the slots 0..E-1: sixteen slot words and K*
+    constexpr int kThr = 16;
+    __shared__ uint32_t s_thr[kThr + 1];
+    __shared__ uint32_t s_cnt[32][kThr + 1];
+    uint32_t tau;  // threshold key: the words with keys at most tau are ranked
+    uint32_t L;
     {
+        if (tid < kThr) s_thr[tid] = 0u;  // a threshold no slot supplies bounds nothing
+        __syncthreads();
         unsigned long long kmax = 0ull;
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             const int idx = tid * KPT + j;
-            if (idx < E) kmax = max(kmax, ((unsigned long long)key[j] << 32) | (uint32_t)idx);
+            if (idx < E) {
+                kmax = max(kmax, w[j]);
+                // slot (i+1) E / kThr - 1 supplies threshold i
+                const int i = (kThr * (idx + 1) + E - 1) / E - 1;
+                if (i >= 0 && i < kThr && idx == (i + 1) * E / kThr - 1)
+                    s_thr[i] = (uint32_t)(w[j] >> 32);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
         if (lane == 0) s_red64[warp] = kmax;
         __syncthreads();
-        if (warp == 0) {
-            unsigned long long v = s_red64[lane];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-            if (lane == 0) {
-                s_kstar = v;
-                s_count = 0;
-            }
+        if (tid == 0) {
+            unsigned long long v = 0ull;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v = max(v, s_red64[w2]);
+            s_thr[kThr] = (uint32_t)(v >> 32);
         }
         __syncthreads();
-    }
-    const unsigned long long kstar = s_kstar;
-    uint32_t nbelow = 0;
+        uint32_t c[kThr + 1];
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        const int idx = tid * KPT + j;
-        nbelow += (idx < P && (((unsigned long long)key[j] << 32) | (uint32_t)idx) <= kstar);
-    }
+        for (int i = 0; i <= kThr; ++i) c[i] = 0;
+        uint32_t thr[kThr + 1];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nbelow += __shfl_xor_sync(0xffffffffu, nbelow, o);
-    if (lane == 0) warp_tot[warp] = nbelow;
-    __syncthreads();
-    uint32_t L = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) L += warp_tot[w];
-    const uint32_t cap = (uint32_t)min(kMaxElite, max(4 * E, 512));
-    if (L <= cap) {
+        for (int i = 0; i <= kThr; ++i) thr[i] = s_thr[i];
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
-            const int idx = tid * KPT + j;
-            const unsigned long long k64 = ((unsigned long long)key[j] << 32) | (uint32_t)idx;
-            const bool take = idx < P && k64 <= kstar;
+            const uint32_t kj = (uint32_t)(w[j] >> 32);
+#pragma unroll
+            for (int i = 0; i <= kThr; ++i) c[i] += kj <= thr[i];
+        }
+#pragma unroll
+        for (int i = 0; i <= kThr; ++i) {
+            c[i] = __reduce_add_sync(0xffffffffu, c[i]);
+            if (lane == 0) s_cnt[warp][i] = c[i];
+        }
+        __syncthreads();
+        if (tid <= kThr) {
+            uint32_t sum = 0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) sum += s_cnt[w2][tid];
+            s_cnt[0][tid] = sum;  // row 0 of column tid is read above by this thread only
+        }
+        __syncthreads();
+        // the threshold bounding the fewest words, but at least E (K* always does)
+        tau = s_thr[kThr];
+        L = s_cnt[0][kThr];
+#pragma unroll
+        for (int i = 0; i < kThr; ++i) {
+            const uint32_t ci = s_cnt[0][i];
+            if (ci >= (uint32_t)E && ci < L) {
+                L = ci;
+                tau = s_thr[i];
+            }
+        }
+    }
+
+    // ---- 2. a sample quantile when none of them admits at most 2048
+    if (L > (uint32_t)kMaxElite) {
+        const int S = min((int)blockDim.x, (P + KPT - 1) / KPT);  // threads holding a word
+        __shared__ uint32_t s_ts;
+        sel[tid] = tid < S ? w[0] : kNone;                        // stride-KPT sample
+        const int r = min(S - 1, (int)((1.25 * E * S) / P) + 8);
+        rank_words(sel, (int)blockDim.x, [&](int rank, unsigned long long x) {
+            if (rank == r) s_ts = (uint32_t)(x >> 32);
+        });
+        __syncthreads();
+        const uint32_t ts = s_ts;
+        const uint32_t Ls = count_at_most<KPT>(w, ts, warp_tot);
+        if (Ls >= (uint32_t)E && Ls <= (uint32_t)kMaxElite) {
+            tau = ts;
+            L = Ls;
+        }
+    }
+
+    if (L <= (uint32_t)kMaxElite) {
+        // ---- compact the words at or below tau, sort, keep the first E
+        if (tid == 0) s_count = 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < KPT; ++j) {
+            const bool take = (uint32_t)(w[j] >> 32) <= tau;
             const uint32_t ball = __ballot_sync(0xffffffffu, take);
             uint32_t base = 0;
             if (lane == 0 && ball) base = atomicAdd(&s_count, (uint32_t)__popc(ball));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) sel[base + __popc(ball & ((1u << lane) - 1u))] = k64;
+            if (take) sel[base + __popc(ball & ((1u << lane) - 1u))] = w[j];
         }
-        __syncthreads();
-        for (int e = tid; e < (int)L; e += blockDim.x) {
-            const unsigned long long mine = sel[e];
-            int rank = 0;
-            for (int f = 0; f < (int)L; ++f) rank += sel[f] < mine;
-            if (rank < E) {
-                const int idx = (int)(mine & 0xFFFFFFFFull);
-                elite_idx[rank] = idx;
-                elite_cost[rank] = cost[idx];
-                if (rank == 0) s_best = idx;
-            }
-        }
-        __syncthreads();
-        finish_select(cost, P, pop, D, best_knots, best_cost, gen, status, s_best);
-        return;
-    }
-
-    // ---- radix select of the E-th smallest key
-    uint32_t prefix = 0, mask = 0, rem = (uint32_t)E;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
-        __syncthreads();
-        // Costs of one population share their leading key bytes, so most
-        // keys hit the same bin: aggregate equal bins within the warp and let
-        // one lane per distinct bin add the count.
+    } else {
+        // ---- 3. exact radix select of the E-th smallest key
+        uint32_t prefix = 0, mask = 0, rem = (uint32_t)E;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            // Costs of one population share their leading key bytes, so most
+            // keys hit the same bin: aggregate equal bins within the warp and
+            // let one lane per distinct bin add the count.
 #pragma unroll
-        for (int j = 0; j < KPT; ++j) {
-            const bool live = tid * KPT + j < P && (key[j] & mask) == prefix;
-            const uint32_t bin = live ? (key[j] >> shift) & 0xFFu : 256u + (threadIdx.x & 31);
-            const uint32_t peers = __match_any_sync(0xffffffffu, bin);
-            if (live && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1))
-                atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-        }
-        __syncthreads();
-        if (tid < 32) {
-            uint32_t loc[8], s = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                loc[b] = hist[tid * 8 + b];
-                s += loc[b];
+            for (int j = 0; j < KPT; ++j) {
+                const uint32_t kj = (uint32_t)(w[j] >> 32);
+                const bool live = w[j] != kNone && (kj & mask) == prefix;
+                const uint32_t bin = live ? (kj >> shift) & 0xFFu : 256u + lane;
+                const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+                if (live && lane == (uint32_t)(__ffs(peers) - 1))
+                    atomicAdd(&hist[bin], (uint32_t)__popc(peers));
             }
-            uint32_t incl = s;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (tid >= o) incl += t;
-            }
-            const uint32_t excl = incl - s;
-            if (excl < rem && rem <= incl) {
-                uint32_t cum = excl;
+            __syncthreads();
+            if (tid < 32) {
+                uint32_t loc[8], sum = 0;
 #pragma unroll
                 for (int b = 0; b < 8; ++b) {
-                    if (cum + loc[b] >= rem) {
-                        s_digit = (uint32_t)(tid * 8 + b);
-                        s_rem = rem - cum;
-                        break;
+                    loc[b] = hist[tid * 8 + b];
+                    sum += loc[b];
+                }
+                uint32_t incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (tid >= o) incl += t;
+                }
+                const uint32_t excl = incl - sum;
+                if (excl < rem && rem <= incl) {
+                    uint32_t cum = excl;
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        if (cum + loc[b] >= rem) {
+                            s_digit = (uint32_t)(tid * 8 + b);
+                            s_rem = rem - cum;
+                            break;
+                        }
+                        cum += loc[b];
                     }
-                    cum += loc[b];
                 }
             }
+            __syncthreads();
+            prefix |= s_digit << shift;
+            mask |= 0xFFu << shift;
+            rem = s_rem;
+            __syncthreads();
         }
-        __syncthreads();
-        prefix |= s_digit << shift;
-        mask |= 0xFFu << shift;
-        rem = s_rem;
-        __syncthreads();
-    }
-    const uint32_t thr = prefix;
-    const uint32_t need_eq = rem;
-
-    // ---- compact: keys below thr, then the first need_eq keys equal to thr
-    uint32_t nless = 0, neq = 0;
+        const uint32_t thr = prefix;
+        const uint32_t need_eq = rem;
+        // keys below thr, then the first need_eq keys equal to thr in index order
+        uint32_t nless = 0, neq = 0;
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        if (tid * KPT + j < P) {
-            nless += key[j] < thr;
-            neq += key[j] == thr;
+        for (int j = 0; j < KPT; ++j) {
+            if (w[j] != kNone) {
+                const uint32_t kj = (uint32_t)(w[j] >> 32);
+                nless += kj < thr;
+                neq += kj == thr;
+            }
         }
-    }
-    const uint32_t packed = block_exclusive_scan((nless << 16) | neq, warp_tot);
-    uint32_t less_before = packed >> 16, eq_before = packed & 0xFFFFu;
+        const uint32_t packed = block_exclusive_scan((nless << 16) | neq, warp_tot);
+        uint32_t less_before = packed >> 16, eq_before = packed & 0xFFFFu;
 #pragma unroll
-    for (int j = 0; j < KPT; ++j) {
-        const int idx = tid * KPT + j;
-        if (idx >= P) continue;
-        const unsigned long long k64 = ((unsigned long long)key[j] << 32) | (uint32_t)idx;
-        if (key[j] < thr) {
-            sel[less_before + min(eq_before, need_eq)] = k64;
-            ++less_before;
-        } else if (key[j] == thr) {
-            if (eq_before < need_eq) sel[less_before + eq_before] = k64;
-            ++eq_before;
+        for (int j = 0; j < KPT; ++j) {
+            if (w[j] == kNone) continue;
+            const uint32_t kj = (uint32_t)(w[j] >> 32);
+            if (kj < thr) {
+                sel[less_before + min(eq_before, need_eq)] = w[j];
+                ++less_before;
+            } else if (kj == thr) {
+                if (eq_before < need_eq) sel[less_before + eq_before] = w[j];
+                ++eq_before;
+            }
         }
+        L = (uint32_t)E;
     }
     __syncthreads();
-
-    // ---- rank by counting and scatter
-    for (int e = tid; e < E; e += blockDim.x) {
-        const unsigned long long mine = sel[e];
-        int rank = 0;
-        for (int f = 0; f < E; ++f) rank += sel[f] < mine;
-        const int idx = (int)(mine & 0xFFFFFFFFull);
-        elite_idx[rank] = idx;
-        elite_cost[rank] = cost[idx];
-        if (rank == 0) s_best = idx;
+    __shared__ int s_best;
+    auto keep = [&](int rank, unsigned long long x) {
+        if (rank < E) {
+            const int idx = (int)(x & 0xFFFFFFFFull);
+            elite_idx[rank] = idx;
+            elite_cost[rank] = __ldcg(cost + idx);
+            if (rank == 0) s_best = idx;
+        }
+    };
+    if (L <= 256u) {
+        // few words: one thread ranks each by counting the words below it
+        // (every thread reads the same word in each iteration: a broadcast)
+        if (tid < (int)L) {
+            const unsigned long long mine = sel[tid];
+            int rank = 0;
+            for (int f = 0; f < (int)L; ++f) rank += sel[f] < mine;
+            keep(rank, mine);
+        }
+    } else {
+        rank_words(sel, (int)L, keep);
     }
     __syncthreads();
     finish_select(cost, P, pop, D, best_knots, best_cost, gen, status, s_best);
@@ -279,6 +415,7 @@ cudaError_t launch_select(const float* cost, int P, int E, const float* pop, int
     if (kpt <= 8) EMPC_SEL(8);
     if (kpt <= 16) EMPC_SEL(16);
     if (kpt <= 32) EMPC_SEL(32);
+    if (kpt <= 64) EMPC_SEL(64);
 #undef EMPC_SEL
     return cudaErrorInvalidValue;
 }

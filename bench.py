@@ -119,17 +119,32 @@ class ClockSampler:
                 "samples": len(inside), "reasons": reasons}
 
 
-def traffic_record(kernel_file):
-    """DRAM bytes per launch from a committed ncu summary, valid only while the
-    kernel source is unchanged (its sha256 is stored beside the figure)."""
+TRAFFIC_SOURCES = {
+    "c2": ["rollout_warp.cu", "rollout_warp.cuh", "rollout_common.cuh", "draws.cuh",
+           "empc_internal.h"],
+    "c5": ["rollout_bf16.cu", "rollout_common.cuh", "draws.cuh", "empc_internal.h"],
+}
+
+
+def sources_sha256(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2001_04931_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_record(workload):
+    """DRAM bytes per rollout launch from a committed ncu capture, valid only
+    while the kernel's sources are unchanged (their sha256 is stored beside
+    the figure)."""
     path = os.path.join(ROOT, "profiles", "rollout_traffic.json")
-    src = os.path.join(ROOT, "paper_2001_04931_gb300", "csrc", kernel_file)
     try:
-        rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return rec if rec.get("source_sha256") == sha else None
-    except (OSError, ValueError):
-        return None
+        rec = json.load(open(path)).get(workload)
+        if rec and rec.get("sources_sha256") == sources_sha256(TRAFFIC_SOURCES[workload]):
+            return rec
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
 
 
 def cpu_baseline(wl, seconds):
@@ -423,12 +438,13 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                 "peak_basis": basis, "flops_per_launch": flops,
                 "mma_flops_per_launch": wl.P * wl.T * 2 * 128 * 192,
                 "launch_us": roll_us, "breed_us": breed_us, "select_us": sel_us,
-                "traffic": None}
+                "traffic": (lambda t: t["dram_bytes_per_launch"] if t else None)(
+                    traffic_record("c5"))}
     else:
         peak, basis, measured = fp32_peak(E, clocks, local_rank)
         flops = alg_flops_per_candidate(wl) * wl.P
         achieved = flops / (roll_us * 1e-6) / 1e12
-        tr = traffic_record("rollout_warp.cuh")
+        tr = traffic_record("c2") if wl.name in ("c2", "c3") else None
         roof = {"bound": "alu", "kernel": "rollout_warp_kernel (knot expansion+rollout+cost)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": basis, "measured_fp32_peak": measured,

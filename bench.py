@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--evaluator", default="rollout", choices=["rollout", "condensed"],
+                    help="population costs by rollout (default) or by the condensed quadratic "
+                         "form of the linear-quadratic problem (c1, c2 only)")
     ap.add_argument("--tile", type=int, default=0,
                     help="1-based rollout tile shape to force (0: autotune); profiling "
                          "runs use it so that the profiled launches match a plain run")
@@ -405,6 +408,9 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
     extra = single_config(wl.name)
     if args.tile:
         extra["tile"] = args.tile
+    condensed = args.evaluator == "condensed"
+    if condensed:
+        extra["evaluator"] = E.EMPC_EVAL_CONDENSED
     prob = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=1 + rank,
                      elite=wl.E, sigma=wl.sigma, **extra)
     prob.set_stream(stream.cuda_stream)
@@ -440,6 +446,17 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                 "launch_us": roll_us, "breed_us": breed_us, "select_us": sel_us,
                 "traffic": (lambda t: t["dram_bytes_per_launch"] if t else None)(
                     traffic_record("c5"))}
+    elif condensed:
+        peak, basis, measured = fp32_peak(E, clocks, local_rank)
+        D = wl.m * wl.p
+        flops = wl.P * (2 * D * D + 4 * D)  # Y = H U, then U'(Y + g)
+        achieved = flops / (roll_us * 1e-6) / 1e12
+        roof = {"bound": "alu", "kernel": "condensed_kernel (J = U'HU + g'U + c0, FP32)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_basis": basis, "measured_fp32_peak": measured,
+                "frac_of_measured": (achieved / measured) if measured else None,
+                "flops_per_launch": flops, "launch_us": roll_us, "breed_us": breed_us,
+                "select_us": sel_us, "traffic": None}
     else:
         peak, basis, measured = fp32_peak(E, clocks, local_rank)
         flops = alg_flops_per_candidate(wl) * wl.P
@@ -457,8 +474,9 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
         compare = compare_refined(E, wl, A, B, prob, x0, g, ms_step)
     if wl.name == "c5":
         compare = compare_bf16(E, wl, A, B, prob, x0, g, ms_step)
-    # per generation: breed, rollout, select (+ the refinement kernel after the first)
-    launches = wl.G * 3 + (wl.G - 1 if wl.name == "c3" else 0)
+    # per generation: breed, rollout, select (+ the refinement kernel after the first;
+    # + one adjoint launch per solve for the condensed terms)
+    launches = wl.G * 3 + (wl.G - 1 if wl.name == "c3" else 0) + (1 if condensed else 0)
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl, args.cpu_seconds)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -50,8 +50,17 @@ typedef enum {
 
 typedef enum { EMPC_FP32 = 0, EMPC_BF16 = 1 } empc_precision;
 
-/* Granularity of the 50% mutation decision (Sec. V: "each input has a 50%
- * probability of being mutated"; Algorithm 1 adds the noise unconditionally). */
+/* How population costs are evaluated.  ROLLOUT simulates every candidate
+ * over the horizon (Sec. V-A).  CONDENSED uses the parameterized small-matrix
+ * form of the linear-quadratic problem (Sec. IV-B, IV-E): J(U) = U'HU + g'U +
+ * c0 with H fixed at create (FP64 on the host, used in FP32) and g = dJ/dU(0),
+ * c0 = J(0) from one adjoint evaluation per solve; the same costs up to
+ * rounding, in 2 (m p)^2 flops per candidate instead of T (2 n^2 + 6 n).
+ * CONDENSED needs FP32, n <= 64, m p <= 832 and no refinement. */
+typedef enum { EMPC_EVAL_ROLLOUT = 0, EMPC_EVAL_CONDENSED = 1 } empc_evaluator;
+
+/* Granularity of the 50% mutation decision (Sec. V gates the mutation per
+ * input with probability one half; Algorithm 1 adds the noise without a gate). */
 typedef enum {
     EMPC_GATE_PER_INPUT = 0, /* one decision per (child, input); all its knots move together */
     EMPC_GATE_PER_KNOT = 1,  /* one decision per (child, knot parameter) */
@@ -70,6 +79,7 @@ typedef struct {
     float refine_lr;     /* step size; 0 = 1/L, L the gradient's Lipschitz constant */
     int ckpt_every;      /* adjoint checkpoint interval; 0 = ceil(sqrt(T)) */
     int tile;            /* 0 = autotune the rollout tile; k > 0 forces candidate shape k-1 */
+    int evaluator;       /* empc_evaluator, default EMPC_EVAL_ROLLOUT */
 } empc_config;
 
 typedef struct {

@@ -21,6 +21,7 @@ EMPC_OK, EMPC_EINVAL, EMPC_ENOMEM, EMPC_ECUDA, EMPC_ETIMEOUT = 0, 1, 2, 3, 4
 EMPC_ENONFINITE, EMPC_ESTATE, EMPC_EUNSUPPORTED = 5, 6, 7
 EMPC_FP32, EMPC_BF16 = 0, 1
 EMPC_GATE_PER_INPUT, EMPC_GATE_PER_KNOT, EMPC_GATE_ALWAYS = 0, 1, 2
+EMPC_EVAL_ROLLOUT, EMPC_EVAL_CONDENSED = 0, 1
 
 _STATUS = {0: "EMPC_OK", 1: "EMPC_EINVAL", 2: "EMPC_ENOMEM", 3: "EMPC_ECUDA",
            4: "EMPC_ETIMEOUT", 5: "EMPC_ENONFINITE", 6: "EMPC_ESTATE",
@@ -32,7 +33,8 @@ class empc_config(ctypes.Structure):
                 ("p_cross_256", ctypes.c_int), ("p_mutate_256", ctypes.c_int),
                 ("gate", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("refine_lr", ctypes.c_float),
-                ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("ckpt_every", ctypes.c_int), ("tile", ctypes.c_int),
+                ("evaluator", ctypes.c_int)]
 
 
 class empc_info(ctypes.Structure):

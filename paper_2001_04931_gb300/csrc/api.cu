@@ -69,6 +69,9 @@ struct empc_problem_s {
     int ce = 1;            // checkpoint interval
     float eta = 0.0f;      // refinement step
     int grad_cands = 1, grad_wpc = 2;
+    // condensed evaluator: J(U) = U'HU + g'U + c0 (H padded to Dp x Dp)
+    int Dp = 0;
+    float *Hc = nullptr, *gvec = nullptr, *c0 = nullptr, *zero_knots = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::string err;
 };
@@ -147,6 +150,33 @@ empc::GradArgs grad_args(empc_handle h) {
     return g;
 }
 
+// Costs of the population a.pop_in into a.cost: the rollout kernel, or the
+// condensed quadratic form (g and c0 of the current start and goal must have
+// been computed by condensed_terms earlier on the stream).
+cudaError_t evaluate_population(empc_handle h, const RolloutArgs& a, cudaStream_t st) {
+    if (h->cfg.evaluator == EMPC_EVAL_CONDENSED) {
+        const empc::CondArgs c{h->Hc, h->gvec, h->c0, a.pop_in, a.cost, h->D, h->Dp, h->P};
+        return empc::launch_condensed(c, st, a.pdl != 0);
+    }
+    return empc::launch_rollout(a, h->shape, st);
+}
+
+// g = dJ/dU at U = 0 and c0 = J(0) for the current start state and goal:
+// one adjoint evaluation of the zero knot vector.
+cudaError_t condensed_terms(empc_handle h, cudaStream_t st) {
+    empc::GradArgs g = grad_args(h);
+    g.x0 = h->x0;
+    g.goal = h->goal;
+    g.pop_in = h->zero_knots;
+    g.ld_in = 1;
+    g.count = 1;
+    g.grad = h->gvec;
+    g.ld_grad = 1;
+    g.cost = h->c0;
+    g.steps = 0;
+    return empc::launch_grad(g, h->shape.nx, h->grad_cands, h->grad_wpc, st);
+}
+
 // One generation into pop[parity^1], then elite selection.  Cold: draw every
 // candidate, then roll out and cost them.  Warm: the fused crossover +
 // mutation kernel breeds the children (slots E..P-1) from the previous
@@ -185,9 +215,9 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
     a.pdl = refine ? 0 : 1;
     e = empc::launch_breed(a, st);
     if (e != cudaSuccess) return e;
-    a.mode = empc::kEval;  // the rollout reads the bred population
+    a.mode = empc::kEval;  // the evaluator reads the bred population
     a.pop_in = h->pop[parity ^ 1];
-    e = empc::launch_rollout(a, h->shape, st);
+    e = evaluate_population(h, a, st);
     if (e != cudaSuccess) return e;
     if (refine && (e = cudaStreamWaitEvent(st, h->ev_join, 0)) != cudaSuccess) return e;
     return empc::launch_select(h->cost, h->P, h->E, h->pop[parity ^ 1], h->D, h->elite_idx,
@@ -195,15 +225,15 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
                                st, !refine);
 }
 
-// Largest eigenvalue of the condensed Hessian H (J = U'HU + 2f'U + c) in
-// FP64, for the projected-gradient step 1/L with L = 2 lambda_max(H).  The
-// columns of S (stacked states x_1..x_T per unit knot, zero x0) come from
-// rollouts of the parameterized dynamics; H = S' Qbig S + sum_k Om_k' R Om_k
-// with Q, R diagonal.  Power iteration.
-double hessian_lambda_max(const double* A, const double* B, const std::vector<double>& qd,
-                          const std::vector<double>& rd, int n, int m, int T, int p,
-                          const std::vector<int>& idx, const std::vector<double>& w0,
-                          const std::vector<double>& w1) {
+// The condensed Hessian H of J = U'HU + 2f'U + c in the knots (Sec. IV-E),
+// FP64, row-major D x D.  The columns of S (stacked states x_1..x_T per unit
+// knot, zero x0) come from rollouts of the parameterized dynamics;
+// H = S' Qbig S + sum_k Om_k' R Om_k with Q, R diagonal.
+std::vector<double> condensed_hessian(const double* A, const double* B,
+                                      const std::vector<double>& qd,
+                                      const std::vector<double>& rd, int n, int m, int T, int p,
+                                      const std::vector<int>& idx, const std::vector<double>& w0,
+                                      const std::vector<double>& w1) {
     const int D = m * p;
     std::vector<double> S((size_t)T * n * D, 0.0), x(n), xn(n);
     for (int q = 0; q < D; ++q) {
@@ -243,6 +273,12 @@ double hessian_lambda_max(const double* A, const double* B, const std::vector<do
                 H[(size_t)b * D + a] += rd[i] * w0[k] * w1[k];
             }
         }
+    return H;
+}
+
+// Largest eigenvalue of the condensed Hessian, for the projected-gradient
+// step 1/L with L = 2 lambda_max(H).  Power iteration.
+double hessian_lambda_max(const std::vector<double>& H, int D) {
     std::vector<double> v(D, 1.0), hv(D);
     double lam = 0.0;
     for (int it = 0; it < 500; ++it) {
@@ -280,6 +316,7 @@ empc_status run_generations(empc_handle h, int G) {
         bool cold = !h->has_pop;
         int parity = h->cur;
         cudaError_t e = cudaSuccess;
+        if (h->cfg.evaluator == EMPC_EVAL_CONDENSED) e = condensed_terms(h, cap);
         for (int g = 0; g < G && e == cudaSuccess; ++g) {
             e = enqueue_generation(h, cold, parity, cap);
             cold = false;
@@ -355,6 +392,14 @@ empc_status autotune(empc_handle h) {
             cudaEventElapsedTime(&ms, e0, e1);
             t_min = std::min(t_min, ms);
         }
+        // a shape whose kernel gave up a bounded wait finished early: not a candidate
+        int st_word = 0;
+        if (good && (cudaMemcpy(&st_word, h->status, sizeof(int), cudaMemcpyDeviceToHost) !=
+                         cudaSuccess ||
+                     st_word != 0)) {
+            good = false;
+            cudaMemset(h->status, 0, sizeof(int));
+        }
         if (!good) {
             cudaGetLastError();
             continue;
@@ -377,7 +422,8 @@ void free_handle(empc_handle h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     void* bufs[] = {h->D_, h->BT, h->qdiag, h->rdiag, h->gram, h->umin, h->umax, h->x0,
                     h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
-                    h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status};
+                    h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
+                    h->Hc, h->gvec, h->c0, h->zero_knots};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->stage) cudaFreeHost(h->stage);
@@ -492,6 +538,7 @@ void empc_config_default(empc_config* cfg) {
     cfg->refine_lr = 0.0f;
     cfg->ckpt_every = 0;
     cfg->tile = 0;
+    cfg->evaluator = EMPC_EVAL_ROLLOUT;
 }
 
 empc_status empc_create(const double* A, const double* B, const double* Q, const double* R,
@@ -526,6 +573,13 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
         return fail(nullptr, EMPC_EINVAL, "need refine_steps >= 0, ckpt_every >= 0, refine_lr >= 0");
     if (cfg.refine_steps > 0 && n > 64)
         return fail(nullptr, EMPC_EUNSUPPORTED, "refinement needs n <= 64");
+    if (cfg.evaluator != EMPC_EVAL_ROLLOUT && cfg.evaluator != EMPC_EVAL_CONDENSED)
+        return fail(nullptr, EMPC_EINVAL, "unknown evaluator");
+    if (cfg.evaluator == EMPC_EVAL_CONDENSED &&
+        (cfg.precision != EMPC_FP32 || n > 64 || cfg.refine_steps > 0 ||
+         !empc::condensed_supported(m * knots)))
+        return fail(nullptr, EMPC_EUNSUPPORTED,
+                    "the condensed evaluator needs FP32, n <= 64, m*p <= 832 and no refinement");
     empc_handle h = new empc_problem_s();
     h->n = n;
     h->m = m;
@@ -578,7 +632,8 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
             std::vector<double> qdd(n), rdd(m);
             for (int i = 0; i < n; ++i) qdd[i] = Q[(size_t)i * n + i];
             for (int i = 0; i < m; ++i) rdd[i] = R[(size_t)i * m + i];
-            const double lmax = hessian_lambda_max(A, B, qdd, rdd, n, m, horizon, knots, idx, w0, w1);
+            const double lmax = hessian_lambda_max(
+                condensed_hessian(A, B, qdd, rdd, n, m, horizon, knots, idx, w0, w1), m * knots);
             h->eta = lmax > 0.0 ? (float)(1.0 / (2.0 * lmax)) : 0.0f;
         }
     }
@@ -618,6 +673,27 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(cudaMemsetAsync(h->goal, 0, sizeof(float) * n, st));
     EMPC_TRY(cudaMemsetAsync(h->gen, 0, sizeof(uint32_t), st));
     EMPC_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    if (cfg.evaluator == EMPC_EVAL_CONDENSED) {
+        std::vector<double> qdd(n), rdd(m);
+        for (int i = 0; i < n; ++i) qdd[i] = Q[(size_t)i * n + i];
+        for (int i = 0; i < m; ++i) rdd[i] = R[(size_t)i * m + i];
+        const std::vector<double> H =
+            condensed_hessian(A, B, qdd, rdd, n, m, horizon, knots, idx, w0, w1);
+        h->Dp = empc::condensed_pad(h->D);
+        std::vector<float> Hf((size_t)h->Dp * h->Dp, 0.0f);
+        for (int a = 0; a < h->D; ++a)
+            for (int b = 0; b < h->D; ++b)
+                Hf[(size_t)a * h->Dp + b] = (float)H[(size_t)a * h->D + b];
+        EMPC_TRY(dev_alloc(&h->Hc, Hf.size()));
+        EMPC_TRY(dev_alloc(&h->gvec, h->Dp));
+        EMPC_TRY(dev_alloc(&h->c0, 1));
+        EMPC_TRY(dev_alloc(&h->zero_knots, D));
+        EMPC_TRY(cudaMemcpyAsync(h->Hc, Hf.data(), sizeof(float) * Hf.size(),
+                                 cudaMemcpyHostToDevice, st));
+        EMPC_TRY(cudaMemsetAsync(h->gvec, 0, sizeof(float) * h->Dp, st));
+        EMPC_TRY(cudaMemsetAsync(h->c0, 0, sizeof(float), st));
+        EMPC_TRY(cudaMemsetAsync(h->zero_knots, 0, sizeof(float) * D, st));
+    }
     EMPC_TRY(cudaStreamSynchronize(st));
 #undef EMPC_TRY
     empc_status s = autotune(h);
@@ -822,7 +898,7 @@ empc_status empc_time_generation(empc_handle h, int reps, float* breed_us, float
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
         a.mode = empc::kEval;
         a.pop_in = h->pop[h->cur ^ 1];
-        if (e == cudaSuccess) e = empc::launch_rollout(a, h->shape, h->stream);
+        if (e == cudaSuccess) e = evaluate_population(h, a, h->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess)
             e = empc::launch_select(h->cost, h->P, h->E, h->pop[h->cur ^ 1], h->D, h->elite_idx,

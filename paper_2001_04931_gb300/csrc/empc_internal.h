@@ -96,11 +96,26 @@ struct GradArgs {
 cudaError_t launch_grad(const GradArgs& a, int nx, int cands, int wpc, cudaStream_t st);
 size_t grad_smem_bytes(int nx, int nrg, int cands, int wpc, int n, int m, int p, int T, int ce);
 
+// Condensed quadratic-form costs J = U'HU + g'U + c0 of a population
+// (condensed.cu).  H is Dp x Dp (zero-padded, symmetric), g and c0 on device.
+struct CondArgs {
+    const float* H;    // [Dp][Dp]
+    const float* g;    // [Dp] (zero past D)
+    const float* c0;   // [1]
+    const float* pop;  // SoA knots [D][P]
+    float* cost;       // [P]
+    int D, Dp, P;
+};
+int condensed_pad(int D);
+bool condensed_supported(int D);
+cudaError_t launch_condensed(const CondArgs& a, cudaStream_t st, bool pdl);
+
 // Fused crossover + mutation (warm) or cold-start draw of candidates
 // cand_begin .. P-1 into pop_out (breed.cu).
 cudaError_t launch_breed(const RolloutArgs& a, cudaStream_t st);
 
 // BF16 tensor-core rollout (rollout_bf16.cu): n <= 128, m <= 64.
+// The product in `groups` (1, 2 or 4) MMA groups; evaluates pop_in (kEval).
 cudaError_t launch_rollout_bf16(const RolloutArgs& a, int groups, cudaStream_t st);
 bool rollout_bf16_supported(int n, int m, int T);
 size_t rollout_bf16_smem_bytes(int T);

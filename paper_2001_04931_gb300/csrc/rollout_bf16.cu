@@ -1,5 +1,6 @@
-// Fused breed + rollout + cost with the per-step product on the tensor cores
-// (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+// Rollout + cost with the per-step product on the tensor cores (tcgen05,
+// BF16 operands, FP32 accumulation in tensor memory); the knots come bred
+// from breed_kernel.
 //
 // For a tile of 128 candidates the step x_{k+1} = x_k + D x_k + B_d u_k
 // (D = A_d - I, Eq. first_order_integration in delta form) is one
@@ -169,6 +170,8 @@ struct Bf16Layout {
     }
 };
 
+// NG: the product issued as NG MMA groups of N = 128 / NG, each committed
+// to its own mbarrier (the autotuner picks NG).
 template <int NG>
 __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const RolloutArgs a) {
     static_assert(NG == 1 || NG == 2 || NG == 4, "MMA groups");
@@ -228,52 +231,14 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         abort_sh = 0;
     }
 
-    // ---- knots: bred (to pop_out) or given (pop_in)
+    // ---- the knots (bred by the previous kernel) are read only after it completed
     pdl_wait_primary();
-    const uint32_t gen = a.gen ? *a.gen : 0u;
-    if (a.mode == kWarm && tid < kTileCands) {
-        int s1, s2;
-        parents_of<false>(a, c0 + tid, gen, s1, s2);
-        par[2 * tid] = s1;
-        par[2 * tid + 1] = s2;
-    }
-    __syncthreads();
-    const int D = m * p;
-    if (a.mode == kWarm) {
-        const int nhex = (D + 15) >> 4;
-        for (int it = tid; it < nhex * kTileCands; it += blockDim.x) {
-            const int t = it % kTileCands, hex = it / kTileCands;
-            const int c = c0 + t;
-            if (c >= a.P) continue;
-            const int s1 = par[2 * t], s2 = par[2 * t + 1];
-            auto emit = [&](int qq, float v) { a.pop_out[(size_t)qq * a.P + c] = v; };
-            if (s2 < 0) {
-                for (int w = 0; w < 16; ++w)
-                    if (hex * 16 + w < D)
-                        emit(hex * 16 + w, __ldcg(a.pop_in + (size_t)(hex * 16 + w) * a.P + s1));
-            } else {
-                breed_hex_warm<false>(a, c, hex, gen, s1, s2, emit);
-            }
-        }
-    } else if (a.mode == kCold) {
-        const int nquad = (D + 3) >> 2;
-        for (int it = tid; it < nquad * kTileCands; it += blockDim.x) {
-            const int t = it % kTileCands, quad = it / kTileCands;
-            const int c = c0 + t;
-            if (c >= a.P) continue;
-            float v[4];
-            breed_quad<false>(a, c, quad, gen, 0, -1, v);
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                if (quad * 4 + w < D) a.pop_out[(size_t)(quad * 4 + w) * a.P + c] = v[w];
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // bred knots visible to the block; TMEM base published
+    __syncthreads();  // TMEM base published
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const float* src = a.mode == kEval ? a.pop_in : a.pop_out;
+    const float* src = a.pop_in;
     const bool live = cand < a.P;
 
     // ---- initial state: FP32 into this thread's chunk of its TMEM lane, BF16 into A[0]
@@ -335,11 +300,21 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
     float2 jacc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
                       make_float2(0.f, 0.f)};
     bool ok = true;
-    int issued = -1;  // last step whose MMAs thread 0 committed
-    const uint32_t idesc = idesc_bf16(kGW);
-    const int grp = q * NG / kChunks;  // the MMA group holding this thread's chunk
+    int issued = -1;  // last step whose MMAs the issuing thread committed
     const float4* g4 = reinterpret_cast<const float4*>(sg + q * kCW);
     const float4* q4 = reinterpret_cast<const float4*>(sq + q * kCW);
+    auto stage_cost = [&](const float (&x)[kCW]) {
+#pragma unroll
+        for (int j = 0; j < kCW; j += 4) {
+            const float4 gg = g4[j / 4], qq = q4[j / 4];
+            const float2 e01 = add2(make_float2(x[j], x[j + 1]), make_float2(-gg.x, -gg.y));
+            const float2 e23 = add2(make_float2(x[j + 2], x[j + 3]), make_float2(-gg.z, -gg.w));
+            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[(j / 4) & 3]);
+            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[(j / 4) & 3]);
+        }
+    };
+    const uint32_t idesc = idesc_bf16(kGW);
+    const int grp = q * NG / kChunks;  // the MMA group holding this thread's chunk
     for (int k = 0; k < T; ++k) {
         uint8_t* Acur = sA[k & 1];
         uint8_t* Anext = sA[(k + 1) & 1];
@@ -356,8 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
 #pragma unroll
                 for (int kk = 0; kk < kK / 16; ++kk) {
                     const uint32_t off = ((kk >> 2) * kAtomBytes + (kk & 3) * 32) >> 4;
-                    mma_bf16(tmem + g * kGW, ad0 + off, bd0 + off + ((g * kGW * 128) >> 4), idesc,
-                             1u);
+                    mma_bf16(tmem + g * kGW, ad0 + off, bd0 + off + ((g * kGW * 128) >> 4),
+                             idesc, 1u);
                 }
                 mma_commit(&mbar[g]);
             }
@@ -374,14 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         float x[kCW];
         tmem_ld32(lane_base + q * kCW, x);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < kCW; j += 4) {
-            const float4 gg = g4[j / 4], qq = q4[j / 4];
-            const float2 e01 = add2(make_float2(x[j], x[j + 1]), make_float2(-gg.x, -gg.y));
-            const float2 e23 = add2(make_float2(x[j + 2], x[j + 3]), make_float2(-gg.z, -gg.w));
-            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[(j / 4) & 3]);
-            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[(j / 4) & 3]);
-        }
+        stage_cost(x);
         if (k + 1 < T) {
 #pragma unroll
             for (int j = 0; j < kCW; j += 8) put8(Anext, row, q * kCW + j, x + j);
@@ -427,22 +395,23 @@ bool rollout_bf16_supported(int n, int m, int T) {
 
 template <int NG>
 cudaError_t launch_groups(const RolloutArgs& a, cudaStream_t st) {
+    auto kern = rollout_bf16_kernel<NG>;
     const size_t smem = rollout_bf16_smem_bytes(a.T);
     static int smem_cap = 48 * 1024;
     if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(rollout_bf16_kernel<NG>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         smem_cap = (int)smem;
     }
     const int grid = (a.P - a.cand_begin + kTileCands - 1) / kTileCands;
     if (grid <= 0) return cudaSuccess;
-    return launch_kernel(rollout_bf16_kernel<NG>, dim3(grid), dim3(kThreads), smem, st,
-                         a.pdl != 0, a);
+    return launch_kernel(kern, dim3(grid), dim3(kThreads), smem, st, a.pdl != 0, a);
 }
 
 cudaError_t launch_rollout_bf16(const RolloutArgs& a, int groups, cudaStream_t st) {
     if (!rollout_bf16_supported(a.n, a.m, a.T)) return cudaErrorInvalidConfiguration;
+    if (a.mode != kEval) return cudaErrorInvalidValue;  // breeding runs in breed_kernel
     switch (groups) {
         case 1: return launch_groups<1>(a, st);
         case 2: return launch_groups<2>(a, st);

@@ -1,7 +1,7 @@
 // Elite selection: the E lowest-cost candidates in (cost, index) order.
 //
-// Algorithm 1's parent line keeps the numParents U arrays with the lowest
-// costs (Sec. V, parent selection).  One CTA of 512 threads per problem.
+// Algorithm 1 keeps the numParents cheapest candidates as the parents of the
+// next generation (Sec. V, parent selection).  One CTA of 512 threads per problem.
 // Each cost maps to an order-preserving 32-bit key (NaN as +inf), paired
 // with its index into a unique 64-bit (key, index) word.  The kernel picks a
 // threshold key tau with at least E and at most 2048 words whose keys are at

@@ -67,11 +67,13 @@ def test_zoh_rejects_bad_input(E):
     dict(Q=np.ones((4, 4))), dict(R=np.array([[1.0, 0.5], [0.5, 1.0]])),
     dict(bounds=np.array([[1.0, -1.0], [-1.0, 1.0]])), dict(A=np.full((4, 4), np.inf)),
     dict(sigma=-1.0), dict(p_cross_256=300), dict(gate=7), dict(Q=-np.eye(4)),
+    dict(evaluator=5), dict(evaluator=1, precision=1), dict(evaluator=1, refine_steps=2),
+    dict(evaluator=1, A=np.eye(66), B=np.ones((66, 2)), Q=np.eye(66)),
 ])
 def test_create_validates_before_touching_the_device(E, bad):
     base = dict(A=np.eye(4), B=np.ones((4, 2)), Q=np.eye(4), R=np.eye(2),
                 bounds=np.tile([-1.0, 1.0], (2, 1)), horizon=50, knots=4, pop=512)
-    cfg_keys = {"elite", "sigma", "p_cross_256", "gate"}
+    cfg_keys = {"elite", "sigma", "p_cross_256", "gate", "evaluator", "precision", "refine_steps"}
     args = {**base, **{k: v for k, v in bad.items() if k not in cfg_keys}}
     cfg = E.default_config(**{k: v for k, v in bad.items() if k in cfg_keys})
     with pytest.raises(E.EmpcError) as ei:
@@ -91,3 +93,4 @@ def test_default_config(E):
     c = E.default_config()
     assert c.sigma == pytest.approx(0.1) and c.p_cross_256 == 128 and c.p_mutate_256 == 128
     assert c.gate == E.EMPC_GATE_PER_INPUT and c.precision == E.EMPC_FP32
+    assert c.evaluator == E.EMPC_EVAL_ROLLOUT

@@ -470,6 +470,9 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                 "select_us": sel_us,
                 "traffic": tr["dram_bytes_per_launch"] if tr else None}
     compare = None
+    loop = None
+    if wl.name in ("c1", "c2") and not condensed:
+        loop = closed_loop_line(E, wl, A, B, 1 + rank, not args.no_cpu_baseline)
     if wl.name == "c3":
         compare = compare_refined(E, wl, A, B, prob, x0, g, ms_step)
     if wl.name == "c5":
@@ -498,7 +501,38 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
         "clocks": clocks,
         "cpu_baseline": cpu,
         **({"compare": compare} if compare else {}),
+        **({"closed_loop": loop} if loop else {}),
     }
+
+
+def closed_loop_line(E, wl, A, B, seed, with_oracle):
+    """Receding-horizon control (empc_closed_loop) of the workload's own plant:
+    50 control steps of 1 and of 3 generations each from x0 toward the goal.
+    Reports the mean time per control step (solve, host copies and the plant
+    update) and the actual cost, beside the FP64 oracle's loop when asked."""
+    out = {"steps": 50}
+    x0, g = wl.start_goal()
+    for G in (1, 3):
+        prob = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=seed,
+                         elite=wl.E, sigma=wl.sigma)
+        prob.closed_loop(A, B, x0, g, 3, G)  # graphs captured, clocks up
+        prob.reset()
+        r = prob.closed_loop(A, B, x0, g, out["steps"], G)
+        prob.close()
+        rec = {"ms_per_step": r["ms_per_step"], "actual_cost": r["actual_cost"],
+               "real_time_100hz": r["ms_per_step"] < 10.0}
+        if with_oracle:
+            import oracle as O
+            Ao, Bo = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+            b = wl.bounds()
+            M = O.Model(Ao, Bo, wl.Q(), wl.R(), b[:, 0], b[:, 1], wl.T, wl.p)
+            ga = O.EMPC(M, wl.P, wl.E, seed=seed, sigma=wl.sigma)
+            ga.gen = 3 * G  # the warm-up steps above advanced the GPU's draw counter
+            _, _, Jo = O.closed_loop(ga, Ao, Bo, wl.Q(), wl.R(), x0, g, out["steps"], G)
+            rec["oracle_actual_cost"] = Jo
+            rec["actual_cost_rel_diff"] = abs(r["actual_cost"] - Jo) / abs(Jo)
+        out[f"generations_{G}"] = rec
+    return out
 
 
 def compare_refined(E, wl, A, B, prob, x0, g, ms_refined):

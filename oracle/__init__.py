@@ -343,3 +343,31 @@ class EMPC:
             self.generation(x0, g)
         best = int(self.elite[0])
         return self.pop[:, best].copy(), float(self.cost[best])
+
+
+def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations):
+    """Receding-horizon control in FP64 (Sec. III-A: solve, apply only the
+    first input, solve again from the state reached; Sec. V: the best input
+    after each solve of `generations` generations).  u_k is the first knot of
+    each input of the best candidate; the plant x_{k+1} = Ad x_k + Bd u_k runs
+    in FP64.  Actual cost (Eq. actual_cost): the stage costs
+    (goal - x_k)' Q (goal - x_k) + u_k' R u_k over the applied steps plus the
+    state term of the final state.  Returns (x [(steps+1), n], u [steps, m],
+    actual cost)."""
+    Ad, Bd, Q, R = _d(Ad), _d(Bd), _d(Q), _d(R)
+    x = _d(x0).copy()
+    goal = _d(goal)
+    p = ga.model.p
+    xs, us, total = [x.copy()], [], 0.0
+    for _ in range(int(steps)):
+        knots, _ = ga.solve(x, goal, generations)
+        u = np.asarray(knots, np.float64)[::p].copy()
+        e = goal - x
+        total += e @ Q @ e + u @ R @ u
+        x = Ad @ x + Bd @ u
+        xs.append(x.copy())
+        us.append(u)
+    e = goal - x
+    total += e @ Q @ e
+    return np.array(xs), np.array(us), float(total)
+

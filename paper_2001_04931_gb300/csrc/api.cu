@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,6 +70,8 @@ struct empc_problem_s {
     int ce = 1;            // checkpoint interval
     float eta = 0.0f;      // refinement step
     int grad_cands = 1, grad_wpc = 2;
+    // diag Q and diag R in FP64 (closed-loop actual cost)
+    std::vector<double> qd_h, rd_h;
     // condensed evaluator: J(U) = U'HU + g'U + c0 (H padded to Dp x Dp)
     int Dp = 0;
     float *Hc = nullptr, *gvec = nullptr, *c0 = nullptr, *zero_knots = nullptr;
@@ -673,6 +676,10 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(cudaMemsetAsync(h->goal, 0, sizeof(float) * n, st));
     EMPC_TRY(cudaMemsetAsync(h->gen, 0, sizeof(uint32_t), st));
     EMPC_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    h->qd_h.resize(n);
+    h->rd_h.resize(m);
+    for (int i = 0; i < n; ++i) h->qd_h[i] = Q[(size_t)i * n + i];
+    for (int i = 0; i < m; ++i) h->rd_h[i] = R[(size_t)i * m + i];
     if (cfg.evaluator == EMPC_EVAL_CONDENSED) {
         std::vector<double> qdd(n), rdd(m);
         for (int i = 0; i < n; ++i) qdd[i] = Q[(size_t)i * n + i];
@@ -751,6 +758,56 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal, in
     std::memcpy(&status_bits, st_out + h->D + 1, sizeof(int));
     if (status_bits & 2) return fail(h, EMPC_ETIMEOUT, "a bounded device wait gave up");
     if (status_bits & 1) return fail(h, EMPC_ENONFINITE, "best cost is not finite");
+    return EMPC_OK;
+}
+
+empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, const double* x0,
+                             const double* x_goal, int steps, int generations, double* x_traj,
+                             double* u_traj, double* actual_cost, double* ms_per_step) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!Ad || !Bd || !x0 || !x_goal || !actual_cost)
+        return fail(h, EMPC_EINVAL, "NULL plant, state, goal or output pointer");
+    if (steps < 1 || generations < 1) return fail(h, EMPC_EINVAL, "need steps, generations >= 1");
+    const int n = h->n, m = h->m, p = h->p;
+    if (!empc::all_finite(Ad, (size_t)n * n) || !empc::all_finite(Bd, (size_t)n * m))
+        return fail(h, EMPC_EINVAL, "non-finite plant matrices");
+    std::vector<double> x(x0, x0 + n), xn(n), u(m);
+    std::vector<float> knots(h->D);
+    auto stage = [&](const double* xs, const double* us) {
+        double J = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double e = x_goal[i] - xs[i];
+            J += h->qd_h[i] * e * e;
+        }
+        if (us)
+            for (int i = 0; i < m; ++i) J += h->rd_h[i] * us[i] * us[i];
+        return J;
+    };
+    double total = 0.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int k = 0; k < steps; ++k) {
+        if (x_traj) std::copy(x.begin(), x.end(), x_traj + (size_t)k * n);
+        float best = 0.0f;
+        const empc_status s = empc_solve(h, x.data(), x_goal, generations, knots.data(), &best);
+        if (s != EMPC_OK) return s;
+        for (int i = 0; i < m; ++i) u[i] = (double)knots[(size_t)i * p];  // u* = U(i, 0)
+        if (u_traj) std::copy(u.begin(), u.end(), u_traj + (size_t)k * m);
+        total += stage(x.data(), u.data());
+        for (int r = 0; r < n; ++r) {
+            double v = 0.0;
+            for (int c = 0; c < n; ++c) v += Ad[(size_t)r * n + c] * x[c];
+            for (int c = 0; c < m; ++c) v += Bd[(size_t)r * m + c] * u[c];
+            xn[r] = v;
+        }
+        x.swap(xn);
+        if (!empc::all_finite(x.data(), n)) return fail(h, EMPC_ENONFINITE, "plant state diverged");
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    if (x_traj) std::copy(x.begin(), x.end(), x_traj + (size_t)steps * n);
+    total += stage(x.data(), nullptr);
+    *actual_cost = total;
+    if (ms_per_step)
+        *ms_per_step = std::chrono::duration<double, std::milli>(t1 - t0).count() / steps;
     return EMPC_OK;
 }
 

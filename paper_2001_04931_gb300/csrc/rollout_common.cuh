@@ -86,16 +86,15 @@ __host__ __device__ __forceinline__ int pair_index(int k, int col, int xs) {
     return ((k >> 1) * xs + col) * 2 + (k & 1);
 }
 
-// Four partial sums of sum_k d[r][k] X[k][c] in two paired accumulators:
-// accA[r][c] = {sum over k = 0 mod 4, sum over k = 1 mod 4},
-// accB[r][c] = {sum over k = 2 mod 4, sum over k = 3 mod 4}, one paired FMA
-// per (row, candidate, k pair).  Four independent chains per output keep the
-// FMA pipe fed; the order is fixed, the same for every candidate.
+// acc[r][c] += sum_k d[r][k] X[k][c] as two partial sums in one paired
+// accumulator: acc.x over even k, acc.y over odd k, one paired FMA per (row,
+// candidate, k pair).  R x C independent paired chains keep the FMA pipe fed
+// (measured: more chains than that lower the packed-FMA rate at two warps
+// per scheduler); the order is fixed, the same for every candidate.
 template <int NX, int R, int C>
 __device__ __forceinline__ void state_product_pairs(const float2 (&d2)[R][NX / 2],
                                                     const float* Xp, int xs,
-                                                    float2 (&accA)[R][C],
-                                                    float2 (&accB)[R][C]) {
+                                                    float2 (&acc)[R][C]) {
 #pragma unroll
     for (int kp = 0; kp < NX / 2; ++kp) {
         float2 xv[C];
@@ -113,10 +112,7 @@ __device__ __forceinline__ void state_product_pairs(const float2 (&d2)[R][NX / 2
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                if (kp & 1) accB[r][c] = fma2(d2[r][kp], xv[c], accB[r][c]);
-                else accA[r][c] = fma2(d2[r][kp], xv[c], accA[r][c]);
-            }
+            for (int c = 0; c < C; ++c) acc[r][c] = fma2(d2[r][kp], xv[c], acc[r][c]);
     }
 }
 

@@ -8,7 +8,7 @@
 // groups per warp).  The warp's state tile lives in its own slice of shared
 // memory, pair-interleaved so one vector load returns rows (k, k+1) of
 // consecutive candidates, and a step needs only a warp barrier.  The sum over
-// k runs as four partial sums with paired FMAs (fma.rn.f32x2).  The
+// k runs as two partial sums with paired FMAs (fma.rn.f32x2).  The
 // per-candidate cost is reduced over the NRG lanes of its group by a
 // butterfly in a fixed order.
 #pragma once
@@ -22,7 +22,7 @@ __host__ __device__ constexpr int nrg_of(int nx) {
 }
 
 // The horizon loop of rollout_common.cuh's horizon_loop on the
-// pair-interleaved state tile, with paired FMAs and four partial sums per
+// pair-interleaved state tile, with paired FMAs and two partial sums per
 // output (state_product_pairs).
 template <int NX, int R, int C>
 __device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
@@ -59,21 +59,19 @@ __device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
             }
             seg = st.idx1;
         }
-        float2 accA[R][C], accB[R][C];
+        float2 acc[R][C];
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                accA[r][c] = make_float2(fmaf(st.w1, bub[r][c], st.w0 * bua[r][c]), 0.0f);
-                accB[r][c] = make_float2(0.0f, 0.0f);
-            }
-        state_product_pairs<NX, R, C>(d2, X + buf * xrows * xs + 2 * col0, xs, accA, accB);
+            for (int c = 0; c < C; ++c)
+                acc[r][c] = make_float2(fmaf(st.w1, bub[r][c], st.w0 * bua[r][c]), 0.0f);
+        state_product_pairs<NX, R, C>(d2, X + buf * xrows * xs + 2 * col0, xs, acc);
         float* Xn = X + (buf ^ 1) * xrows * xs;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const float sum = (accA[r][c].x + accB[r][c].x) + (accA[r][c].y + accB[r][c].y);
+                const float sum = acc[r][c].x + acc[r][c].y;
                 const float xn = xo[r][c] + sum;
                 xo[r][c] = xn;
                 const float e = xn - gl[r];

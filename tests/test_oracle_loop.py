@@ -1,0 +1,62 @@
+"""Pins for the oracle's receding-horizon loop (Sec. III-A, Sec. V; actual
+cost by Eq. actual_cost): a plant that inputs cannot move gives a closed-form
+actual cost, the first applied input is the first knot of the first solve's
+best candidate, and on a chain that starts away from its goal the loop beats
+applying no input at all."""
+import numpy as np
+
+import oracle as O
+import workloads as W
+from helpers import oracle_model
+
+
+def _setup(**kw):
+    wl = W.small(dof=2, T=20, p=3, P=120, E=10, **kw)
+    M = oracle_model(wl)
+    A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+    return wl, M, A, B
+
+
+def test_frozen_plant_actual_cost_closed_form():
+    wl, M, A, B = _setup()
+    x0, g = wl.start_goal()
+    ga = O.EMPC(M, wl.P, wl.E, seed=3, sigma=wl.sigma)
+    steps = 6
+    xs, us, J = O.closed_loop(ga, np.eye(wl.n), np.zeros((wl.n, wl.m)), wl.Q(), wl.R(), x0, g,
+                              steps, 2)
+    np.testing.assert_array_equal(xs, np.tile(x0, (steps + 1, 1)))
+    e = g - x0
+    state_term = e @ wl.Q() @ e
+    input_term = sum(u @ wl.R() @ u for u in us)
+    assert abs(J - ((steps + 1) * state_term + input_term)) <= 1e-12 * J
+
+
+def test_first_input_is_first_knot_of_best():
+    wl, M, A, B = _setup()
+    x0, g = wl.start_goal()
+    ga = O.EMPC(M, wl.P, wl.E, seed=4, sigma=wl.sigma)
+    ref = O.EMPC(M, wl.P, wl.E, seed=4, sigma=wl.sigma)
+    knots, _ = ref.solve(x0, g, 3)
+    xs, us, _ = O.closed_loop(ga, A, B, wl.Q(), wl.R(), x0, g, 1, 3)
+    np.testing.assert_array_equal(us[0], knots.astype(np.float64)[::wl.p])
+    np.testing.assert_allclose(xs[1], A @ x0 + B @ us[0], rtol=0, atol=0)
+
+
+def test_loop_beats_no_input():
+    wl = W.small(dof=2, T=60, p=3, P=200, E=12)
+    M = oracle_model(wl)
+    A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+    x0 = np.zeros(wl.n)
+    g = np.r_[np.full(wl.dof, 0.05), np.zeros(wl.dof)]  # holdable within the input bounds
+    ga = O.EMPC(M, wl.P, wl.E, seed=5, sigma=wl.sigma)
+    steps = 300
+    xs, _, J = O.closed_loop(ga, A, B, wl.Q(), wl.R(), x0, g, steps, 2)
+    x, J0 = x0.copy(), 0.0
+    for _ in range(steps):
+        e = g - x
+        J0 += e @ wl.Q() @ e
+        x = A @ x
+    e = g - x
+    J0 += e @ wl.Q() @ e
+    assert J < 0.5 * J0
+    assert np.abs(xs[-1] - g).max() < 0.2 * np.abs(x0 - g).max()

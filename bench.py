@@ -528,7 +528,7 @@ def closed_loop_line(E, wl, A, B, seed, with_oracle):
             M = O.Model(Ao, Bo, wl.Q(), wl.R(), b[:, 0], b[:, 1], wl.T, wl.p)
             ga = O.EMPC(M, wl.P, wl.E, seed=seed, sigma=wl.sigma)
             ga.gen = 3 * G  # the warm-up steps above advanced the GPU's draw counter
-            _, _, Jo = O.closed_loop(ga, Ao, Bo, wl.Q(), wl.R(), x0, g, out["steps"], G)
+            _, _, Jo, _ = O.closed_loop(ga, Ao, Bo, wl.Q(), wl.R(), x0, g, out["steps"], G)
             rec["oracle_actual_cost"] = Jo
             rec["actual_cost_rel_diff"] = abs(r["actual_cost"] - Jo) / abs(Jo)
         out[f"generations_{G}"] = rec

@@ -129,6 +129,13 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal,
                        int generations, float* best_knots, float* best_cost);
 
 /*
+ * empc_set_sigma - the standard deviation of the mutation noise used from
+ * the next generation on (initially empc_config.sigma).  Stream-ordered on
+ * the handle's stream; EMPC_EINVAL unless finite and >= 0.
+ */
+empc_status empc_set_sigma(empc_handle h, float sigma);
+
+/*
  * empc_closed_loop - receding-horizon control of a plant (Sec. III-A: solve,
  * apply only the first input, solve again from the new state; Sec. V: EMPC
  * applies the best input after each solve of `generations` generations).
@@ -137,16 +144,21 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal,
  * candidate), and the plant advances in FP64 on the host:
  * x_{k+1} = Ad x_k + Bd u_k.  Ad [n*n] and Bd [n*m] (row-major, host FP64)
  * are the plant, which may differ from the model given to empc_create
- * (model error).  Outputs: actual_cost (Eq. actual_cost) =
- * sum_k (x_goal - x_k)' Q (x_goal - x_k) + u_k' R u_k over the applied steps
- * plus the state term of the final state x_steps; optional x_traj
- * [(steps+1)*n], u_traj [steps*m] and the mean wall time per step in ms
- * (solve plus plant update).  Errors as empc_solve; EMPC_ENONFINITE if the
- * plant state diverges.
+ * (model error).  With sigma_dref > 0 the mutation noise depends on the
+ * distance to the goal (Sec. VII: exploration that shrinks near the goal
+ * keeps the system there): sigma_k = max(sigma_min, sigma min(1, |x_k - g| /
+ * sigma_dref)), |.| the Euclidean norm summed in index order in FP64 and
+ * sigma the configured one; sigma is restored afterwards.  Outputs:
+ * actual_cost (Eq. actual_cost) = sum_k (x_goal - x_k)' Q (x_goal - x_k) +
+ * u_k' R u_k over the applied steps plus the state term of the final state
+ * x_steps; optional x_traj [(steps+1)*n], u_traj [steps*m] and the mean
+ * wall time per step in ms (solve plus plant update).  Errors as empc_solve;
+ * EMPC_ENONFINITE if the plant state diverges.
  */
 empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, const double* x0,
-                             const double* x_goal, int steps, int generations, double* x_traj,
-                             double* u_traj, double* actual_cost, double* ms_per_step);
+                             const double* x_goal, int steps, int generations, double sigma_min,
+                             double sigma_dref, double* x_traj, double* u_traj,
+                             double* actual_cost, double* ms_per_step);
 
 /*
  * empc_solve_device - as empc_solve with device inputs and outputs:

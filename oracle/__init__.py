@@ -345,21 +345,31 @@ class EMPC:
         return self.pop[:, best].copy(), float(self.cost[best])
 
 
-def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations):
+def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations, sigma_min=0.0, sigma_dref=0.0):
     """Receding-horizon control in FP64 (Sec. III-A: solve, apply only the
     first input, solve again from the state reached; Sec. V: the best input
     after each solve of `generations` generations).  u_k is the first knot of
     each input of the best candidate; the plant x_{k+1} = Ad x_k + Bd u_k runs
-    in FP64.  Actual cost (Eq. actual_cost): the stage costs
-    (goal - x_k)' Q (goal - x_k) + u_k' R u_k over the applied steps plus the
-    state term of the final state.  Returns (x [(steps+1), n], u [steps, m],
-    actual cost)."""
+    in FP64.  With sigma_dref > 0 the mutation sigma depends on the distance
+    to the goal (Sec. VII): sigma_k = max(sigma_min, sigma0 min(1, |x_k - g| /
+    sigma_dref)) with sigma0 the EMPC object's (FP32) sigma and the norm
+    summed in index order, rounded to FP32.  Actual cost (Eq. actual_cost):
+    the stage costs (goal - x_k)' Q (goal - x_k) + u_k' R u_k over the applied
+    steps plus the state term of the final state.  Returns (x [(steps+1), n],
+    u [steps, m], actual cost, sigmas [steps])."""
     Ad, Bd, Q, R = _d(Ad), _d(Bd), _d(Q), _d(R)
     x = _d(x0).copy()
     goal = _d(goal)
     p = ga.model.p
-    xs, us, total = [x.copy()], [], 0.0
+    sigma0 = float(np.float32(ga.sigma))
+    xs, us, sig, total = [x.copy()], [], [], 0.0
     for _ in range(int(steps)):
+        if sigma_dref > 0.0:
+            d2 = 0.0
+            for v in (x - goal):
+                d2 += float(v) * float(v)
+            ga.sigma = float(np.float32(max(sigma_min, sigma0 * min(1.0, np.sqrt(d2) / sigma_dref))))
+        sig.append(ga.sigma)
         knots, _ = ga.solve(x, goal, generations)
         u = np.asarray(knots, np.float64)[::p].copy()
         e = goal - x
@@ -367,7 +377,7 @@ def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations):
         x = Ad @ x + Bd @ u
         xs.append(x.copy())
         us.append(u)
+    ga.sigma = sigma0
     e = goal - x
     total += e @ Q @ e
-    return np.array(xs), np.array(us), float(total)
-
+    return np.array(xs), np.array(us), float(total), np.array(sig)

@@ -91,7 +91,9 @@ _SIGNATURES = {
     "empc_last_error": (ctypes.c_char_p, [_h]),
     "empc_discretize_zoh": (_i, [_dp, _dp, _i, _i, ctypes.c_double, _dp, _dp]),
     "empc_time_generation": (_i, [_h, _i, _fp, _fp, _fp]),
-    "empc_closed_loop": (_i, [_h, _dp, _dp, _dp, _dp, _i, _i, _dp, _dp, _dp, _dp]),
+    "empc_closed_loop": (_i, [_h, _dp, _dp, _dp, _dp, _i, _i, ctypes.c_double, ctypes.c_double,
+                              _dp, _dp, _dp, _dp]),
+    "empc_set_sigma": (_i, [_h, ctypes.c_float]),
     "empc_measure_fp32_peak": (_i, [_dp]),
     "empc_evaluate_noalloc": (_i, [_dp, _dp, _dp, _dp, _i, _i, _i, _i, _vp, _vp, _vp, _i,
                                   _vp, _vp]),
@@ -259,18 +261,24 @@ class Problem:
     def reset(self):
         check(_lib.empc_reset(self.handle), self.handle)
 
-    def closed_loop(self, Ad, Bd, x0, x_goal, steps, generations):
+    def set_sigma(self, sigma):
+        check(_lib.empc_set_sigma(self.handle, float(sigma)), self.handle)
+
+    def closed_loop(self, Ad, Bd, x0, x_goal, steps, generations, sigma_min=0.0,
+                    sigma_dref=0.0):
         """Receding-horizon control of the plant (Ad, Bd) for `steps` steps of
-        `generations` generations each: dict(x [(steps+1), n], u [steps, m],
-        actual_cost, ms_per_step)."""
+        `generations` generations each (sigma_dref > 0: mutation sigma scaled
+        by the distance to the goal, at least sigma_min): dict(x [(steps+1), n],
+        u [steps, m], actual_cost, ms_per_step)."""
         Ad, Bd = _d(Ad), _d(Bd)
         x0, g = _d(x0), _d(x_goal)
         xt = np.zeros((int(steps) + 1, self.n))
         ut = np.zeros((int(steps), self.m))
         cost, ms = ctypes.c_double(), ctypes.c_double()
         check(_lib.empc_closed_loop(self.handle, _ptr(Ad), _ptr(Bd), _ptr(x0), _ptr(g),
-                                    int(steps), int(generations), _ptr(xt), _ptr(ut),
-                                    ctypes.byref(cost), ctypes.byref(ms)), self.handle)
+                                    int(steps), int(generations), float(sigma_min),
+                                    float(sigma_dref), _ptr(xt), _ptr(ut), ctypes.byref(cost),
+                                    ctypes.byref(ms)), self.handle)
         return {"x": xt, "u": ut, "actual_cost": cost.value, "ms_per_step": ms.value}
 
     def time_generation(self, reps):

@@ -70,6 +70,8 @@ struct empc_problem_s {
     int ce = 1;            // checkpoint interval
     float eta = 0.0f;      // refinement step
     int grad_cands = 1, grad_wpc = 2;
+    float* sigma_dev = nullptr;  // the mutation sigma the breeding kernel reads
+    float sigma_now = 0.0f;      // host copy being transferred to sigma_dev
     // diag Q and diag R in FP64 (closed-loop actual cost)
     std::vector<double> qd_h, rd_h;
     // condensed evaluator: J(U) = U'HU + g'U + c0 (H padded to Dp x Dp)
@@ -125,6 +127,7 @@ RolloutArgs base_args(empc_handle h) {
     a.seed = h->cfg.seed;
     a.gen = h->gen;
     a.sigma = h->cfg.sigma;
+    a.sigma_dev = h->sigma_dev;
     a.pc256 = h->cfg.p_cross_256;
     a.pm256 = h->cfg.p_mutate_256;
     a.gate = h->cfg.gate;
@@ -426,7 +429,7 @@ void free_handle(empc_handle h) {
     void* bufs[] = {h->D_, h->BT, h->qdiag, h->rdiag, h->gram, h->umin, h->umax, h->x0,
                     h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
                     h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
-                    h->Hc, h->gvec, h->c0, h->zero_knots};
+                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->stage) cudaFreeHost(h->stage);
@@ -661,6 +664,7 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(dev_alloc(&h->best_cost, 1));
     EMPC_TRY(dev_alloc(&h->gen, 1));
     EMPC_TRY(dev_alloc(&h->status, 1));
+    EMPC_TRY(dev_alloc(&h->sigma_dev, 1));
     EMPC_TRY(cudaMallocHost(reinterpret_cast<void**>(&h->stage),
                             sizeof(float) * (2 * (size_t)n + D + 2)));
     cudaStream_t st = h->stream;
@@ -676,6 +680,7 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(cudaMemsetAsync(h->goal, 0, sizeof(float) * n, st));
     EMPC_TRY(cudaMemsetAsync(h->gen, 0, sizeof(uint32_t), st));
     EMPC_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    EMPC_TRY(cudaMemcpyAsync(h->sigma_dev, &h->cfg.sigma, sizeof(float), cudaMemcpyHostToDevice, st));
     h->qd_h.resize(n);
     h->rd_h.resize(m);
     for (int i = 0; i < n; ++i) h->qd_h[i] = Q[(size_t)i * n + i];
@@ -761,13 +766,26 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal, in
     return EMPC_OK;
 }
 
+empc_status empc_set_sigma(empc_handle h, float sigma) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (!(sigma >= 0.0f) || !std::isfinite(sigma)) return fail(h, EMPC_EINVAL, "need sigma >= 0");
+    h->sigma_now = sigma;
+    EMPC_CUDA(h, cudaMemcpyAsync(h->sigma_dev, &h->sigma_now, sizeof(float),
+                                 cudaMemcpyHostToDevice, h->stream));
+    return EMPC_OK;
+}
+
 empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, const double* x0,
-                             const double* x_goal, int steps, int generations, double* x_traj,
-                             double* u_traj, double* actual_cost, double* ms_per_step) {
+                             const double* x_goal, int steps, int generations, double sigma_min,
+                             double sigma_dref, double* x_traj, double* u_traj,
+                             double* actual_cost, double* ms_per_step) {
     if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
     if (!Ad || !Bd || !x0 || !x_goal || !actual_cost)
         return fail(h, EMPC_EINVAL, "NULL plant, state, goal or output pointer");
     if (steps < 1 || generations < 1) return fail(h, EMPC_EINVAL, "need steps, generations >= 1");
+    if (!(sigma_min >= 0.0) || !(sigma_dref >= 0.0) || !std::isfinite(sigma_min) ||
+        !std::isfinite(sigma_dref))
+        return fail(h, EMPC_EINVAL, "need finite sigma_min, sigma_dref >= 0");
     const int n = h->n, m = h->m, p = h->p;
     if (!empc::all_finite(Ad, (size_t)n * n) || !empc::all_finite(Bd, (size_t)n * m))
         return fail(h, EMPC_EINVAL, "non-finite plant matrices");
@@ -787,6 +805,15 @@ empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, 
     const auto t0 = std::chrono::steady_clock::now();
     for (int k = 0; k < steps; ++k) {
         if (x_traj) std::copy(x.begin(), x.end(), x_traj + (size_t)k * n);
+        if (sigma_dref > 0.0) {
+            // exploration shrinks near the goal: sigma0 min(1, |x - g| / dref), at least sigma_min
+            double d2 = 0.0;
+            for (int i = 0; i < n; ++i) d2 += (x[i] - x_goal[i]) * (x[i] - x_goal[i]);
+            const double sg = std::max(
+                sigma_min, (double)h->cfg.sigma * std::min(1.0, std::sqrt(d2) / sigma_dref));
+            const empc_status s = empc_set_sigma(h, (float)sg);
+            if (s != EMPC_OK) return s;
+        }
         float best = 0.0f;
         const empc_status s = empc_solve(h, x.data(), x_goal, generations, knots.data(), &best);
         if (s != EMPC_OK) return s;
@@ -803,6 +830,10 @@ empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, 
         if (!empc::all_finite(x.data(), n)) return fail(h, EMPC_ENONFINITE, "plant state diverged");
     }
     const auto t1 = std::chrono::steady_clock::now();
+    if (sigma_dref > 0.0) {  // back to the configured sigma
+        const empc_status s = empc_set_sigma(h, h->cfg.sigma);
+        if (s != EMPC_OK) return s;
+    }
     if (x_traj) std::copy(x.begin(), x.end(), x_traj + (size_t)steps * n);
     total += stage(x.data(), nullptr);
     *actual_cost = total;

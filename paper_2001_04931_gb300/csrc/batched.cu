@@ -712,6 +712,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         a.seed = d.seed;
         a.gen = reinterpret_cast<uint32_t*>(base + o.gen);
         a.sigma = d.sigma > 0.0f ? d.sigma : cfg.sigma;
+        a.sigma_dev = nullptr;
         a.pc256 = cfg.p_cross_256;
         a.pm256 = cfg.p_mutate_256;
         a.gate = cfg.gate;

@@ -42,6 +42,7 @@ struct RolloutArgs {
     uint64_t seed;
     const uint32_t* gen;  // device generation counter
     float sigma;
+    const float* sigma_dev;  // if set, the mutation sigma is read here (set per solve)
     int pc256, pm256, gate;
     int cand_begin;  // first candidate this launch covers (later ones up to P)
     int pdl;         // launch with programmatic stream serialization

@@ -155,6 +155,12 @@ __device__ __forceinline__ float pop_load(const float* p) {
     return __ldcg(p);
 }
 
+// The mutation's standard deviation: per solve from device memory when the
+// host sets it (distance-dependent exploration), else the fixed one.
+__device__ __forceinline__ float noise_sigma(const RolloutArgs& a) {
+    return a.sigma_dev ? __ldcg(a.sigma_dev) : a.sigma;
+}
+
 // Parents of child c as population columns (s1, s2); s2 < 0 marks an elite
 // slot (c < E) copied unchanged from column s1.  Warm start only.
 template <bool COHERENT>
@@ -247,7 +253,7 @@ __device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad
                         gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
                         have_z = true;
                     }
-                    val = __fmaf_rn(a.sigma, z[w], mate[w]);
+                    val = __fmaf_rn(noise_sigma(a), z[w], mate[w]);
                 }
                 v[w] = clamp_to(val, a.umin[i], a.umax[i]);
             }
@@ -309,7 +315,7 @@ __device__ __forceinline__ void breed_hex_warm(const RolloutArgs& a, int c, int 
                     gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
                     have_z = true;
                 }
-                val = __fmaf_rn(a.sigma, z[w], mate[w]);
+                val = __fmaf_rn(noise_sigma(a), z[w], mate[w]);
             }
             emit(q, clamp_to(val, a.umin[i], a.umax[i]));
         }

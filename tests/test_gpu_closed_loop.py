@@ -24,7 +24,7 @@ def test_closed_loop_matches_oracle_loop():
     prob = gpu_problem(wl, seed=6)
     out = prob.closed_loop(A, B, x0, g, steps, G)
     ga = O.EMPC(oracle_model(wl), wl.P, wl.E, seed=6, sigma=wl.sigma)
-    xs, us, J = O.closed_loop(ga, A, B, wl.Q(), wl.R(), x0, g, steps, G)
+    xs, us, J, _ = O.closed_loop(ga, A, B, wl.Q(), wl.R(), x0, g, steps, G)
     np.testing.assert_array_equal(out["u"][0], us[0])
     # the library's bookkeeping, recomputed from its own trajectory
     Q, R = wl.Q(), wl.R()
@@ -34,6 +34,23 @@ def test_closed_loop_matches_oracle_loop():
                                rtol=0, atol=1e-12)
     assert abs(out["actual_cost"] - J) <= 1e-3 * J
     assert out["ms_per_step"] > 0
+    prob.close()
+
+
+def test_closed_loop_distance_scaled_sigma_matches_oracle():
+    wl = W.small(dof=2, T=20, p=3, P=200, E=12)
+    x0 = np.zeros(wl.n)
+    g = np.r_[np.full(wl.dof, 0.05), np.zeros(wl.dof)]
+    A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+    steps, G = 20, 2
+    prob = gpu_problem(wl, seed=7)
+    out = prob.closed_loop(A, B, x0, g, steps, G, sigma_min=0.005, sigma_dref=0.5)
+    ga = O.EMPC(oracle_model(wl), wl.P, wl.E, seed=7, sigma=wl.sigma)
+    xs, us, J, sig = O.closed_loop(ga, A, B, wl.Q(), wl.R(), x0, g, steps, G, sigma_min=0.005,
+                                   sigma_dref=0.5)
+    assert sig[0] < np.float32(wl.sigma)  # the schedule is active from the first step
+    np.testing.assert_array_equal(out["u"][0], us[0])
+    assert abs(out["actual_cost"] - J) <= 1e-3 * J
     prob.close()
 
 
@@ -47,5 +64,11 @@ def test_closed_loop_rejects_bad_arguments():
     assert ei.value.status == E.EMPC_EINVAL
     with pytest.raises(E.EmpcError) as ei:
         prob.closed_loop(np.full_like(A, np.nan), B, np.zeros(wl.n), np.zeros(wl.n), 3, 1)
+    assert ei.value.status == E.EMPC_EINVAL
+    with pytest.raises(E.EmpcError) as ei:
+        prob.closed_loop(A, B, np.zeros(wl.n), np.zeros(wl.n), 3, 1, sigma_dref=-1.0)
+    assert ei.value.status == E.EMPC_EINVAL
+    with pytest.raises(E.EmpcError) as ei:
+        prob.set_sigma(-0.5)
     assert ei.value.status == E.EMPC_EINVAL
     prob.close()

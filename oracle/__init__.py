@@ -55,6 +55,14 @@ def lib():
         L.orc_cost_population.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp, _fp,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+        L.orc_cost_box.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                   ctypes.c_int, _dp]
+        L.orc_cost_box.restype = ctypes.c_double
+        L.orc_cost_population_box.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp, _fp,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                              ctypes.c_int, _dp]
         L.orc_condensed.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                     _dp, _dp]
@@ -138,6 +146,28 @@ def expand(U, m, T, p):
     return out
 
 
+class StateBox:
+    """The state-box hook (Sec. V: with every state of every step simulated,
+    effects such as hard stops and non-convex state costs go into the
+    simulation as plain if/else).  Per state i: bounds lo_i <= hi_i and weight
+    rho_i >= 0.  After each update, d_i = max(0, lo_i - x_i, x_i - hi_i);
+    `penalty` adds rho_i d_i^2 to the cost, `clamp` stops the state at the
+    box.  Both act before the stage cost, which sees the stopped state."""
+
+    def __init__(self, lo, hi, rho=None, clamp=False, penalty=False):
+        self.lo = _d(lo)
+        self.hi = _d(hi)
+        self.rho = np.zeros_like(self.lo) if rho is None else _d(rho)
+        self.mode = (1 if clamp else 0) | (2 if penalty else 0)
+
+    def _args(self):
+        return _ptr(self.lo, _dp), _ptr(self.hi, _dp), _ptr(self.rho, _dp), self.mode
+
+    def stop(self, x):
+        """The hard stop applied to a plant state (identity without clamp)."""
+        return np.minimum(np.maximum(x, self.lo), self.hi) if self.mode & 1 else x
+
+
 class Model:
     """Discrete model and cost weights, all FP64 (row-major)."""
 
@@ -158,23 +188,39 @@ class Model:
         return (_ptr(self.A, _dp), _ptr(self.B, _dp), _ptr(self.Q, _dp),
                 _ptr(self.R, _dp), self._wp)
 
-    def cost(self, x0, g, U, conv=0, return_traj=False):
+    def cost(self, x0, g, U, conv=0, return_traj=False, box=None):
+        """J(U) (and x_0..x_T); with a StateBox, the hooked simulation
+        (conv 0 only)."""
         x0, g, U = _d(x0), _d(g), _d(U)
         traj = np.zeros((self.T + 1, self.n)) if return_traj else None
-        J = lib().orc_cost(*self._mats(), _ptr(x0, _dp), _ptr(g, _dp), _ptr(U, _dp),
-                           self.n, self.m, self.T, self.p, conv,
-                           _ptr(traj, _dp) if return_traj else None)
+        tp = _ptr(traj, _dp) if return_traj else None
+        if box is None:
+            J = lib().orc_cost(*self._mats(), _ptr(x0, _dp), _ptr(g, _dp), _ptr(U, _dp),
+                               self.n, self.m, self.T, self.p, conv, tp)
+        else:
+            if conv != 0:
+                raise ValueError("the state-box hook follows cost convention 0")
+            J = lib().orc_cost_box(*self._mats(), _ptr(x0, _dp), _ptr(g, _dp),
+                                   _ptr(U, _dp), self.n, self.m, self.T, self.p,
+                                   *box._args(), tp)
         return (J, traj) if return_traj else J
 
-    def cost_population(self, x0, g, pop, conv=0):
+    def cost_population(self, x0, g, pop, conv=0, box=None):
         """FP64 costs of an SoA FP32 population pop[m*p, P]."""
         x0, g = _d(x0), _d(g)
         pop = np.ascontiguousarray(pop, dtype=np.float32)
         P = pop.shape[1]
         out = np.zeros(P)
-        lib().orc_cost_population(*self._mats(), _ptr(x0, _dp), _ptr(g, _dp),
-                                  _ptr(pop, _fp), self.n, self.m, self.T, self.p, P, conv,
-                                  _ptr(out, _dp))
+        if box is None:
+            lib().orc_cost_population(*self._mats(), _ptr(x0, _dp), _ptr(g, _dp),
+                                      _ptr(pop, _fp), self.n, self.m, self.T, self.p, P,
+                                      conv, _ptr(out, _dp))
+        else:
+            if conv != 0:
+                raise ValueError("the state-box hook follows cost convention 0")
+            lib().orc_cost_population_box(*self._mats(), _ptr(x0, _dp), _ptr(g, _dp),
+                                          _ptr(pop, _fp), self.n, self.m, self.T, self.p,
+                                          P, *box._args(), _ptr(out, _dp))
         return out
 
     def condensed(self, x0, g, return_S=False):
@@ -293,8 +339,9 @@ class EMPC:
     """
 
     def __init__(self, model, P, E, seed, sigma, pc256=128, pm256=128, gate_mode=0,
-                 refine_steps=0, refine_eta=0.0):
+                 refine_steps=0, refine_eta=0.0, box=None):
         self.model = model
+        self.box = box
         self.P, self.E = int(P), int(E)
         self.seed = int(seed)
         self.sigma = float(sigma)
@@ -335,7 +382,7 @@ class EMPC:
                 pop[:, :self.E] = self.refined_elites(x0, g).astype(np.float32)
         self.gen += 1
         self.pop = pop
-        self.cost = M.cost_population(x0, g, pop)
+        self.cost = M.cost_population(x0, g, pop, box=self.box)
         self.elite = select(self.cost, self.E)
 
     def solve(self, x0, g, generations):
@@ -355,8 +402,10 @@ def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations, sigma_min=0.0, s
     sigma_dref)) with sigma0 the EMPC object's (FP32) sigma and the norm
     summed in index order, rounded to FP32.  Actual cost (Eq. actual_cost):
     the stage costs (goal - x_k)' Q (goal - x_k) + u_k' R u_k over the applied
-    steps plus the state term of the final state.  Returns (x [(steps+1), n],
-    u [steps, m], actual cost, sigmas [steps])."""
+    steps plus the state term of the final state.  With the EMPC object's
+    StateBox set to clamp, the plant is stopped at the same box after every
+    step.  Returns (x [(steps+1), n], u [steps, m], actual cost, sigmas
+    [steps])."""
     Ad, Bd, Q, R = _d(Ad), _d(Bd), _d(Q), _d(R)
     x = _d(x0).copy()
     goal = _d(goal)
@@ -375,6 +424,8 @@ def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations, sigma_min=0.0, s
         e = goal - x
         total += e @ Q @ e + u @ R @ u
         x = Ad @ x + Bd @ u
+        if ga.box is not None:
+            x = ga.box.stop(x)
         xs.append(x.copy())
         us.append(u)
     ga.sigma = sigma0

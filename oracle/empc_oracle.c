@@ -34,6 +34,8 @@
  *   orc_condensed          parameterized small-matrix formulation
  *                          J = U'HU + 2f'U + c (Sec. IV-B and IV-E).
  *   orc_grad               adjoint gradient dJ/dU (no counterpart in the paper).
+ *   orc_cost_box           orc_cost (conv 0) with the state-box hook of Sec. V:
+ *                          hinge penalty and/or hard stop per state.
  *   orc_select             parent selection: the lowest-cost candidates (Alg. 1
  *                          parent line, Sec. V parent selection).
  *   orc_breed_cold/_warm   cold start and mate + mutate (Alg. 1, Sec. V).
@@ -377,6 +379,83 @@ ORC_EXPORT void orc_cost_population(const double* A, const double* B, const doub
         double* U = (double*)malloc(sizeof(double) * (size_t)D);
         for (int q = 0; q < D; ++q) U[q] = (double)pop[(size_t)q * P + c];
         cost[c] = orc_cost(A, B, Q, R, w, x0, g, U, n, m, T, p, conv, NULL);
+        free(U);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward simulation with the state-box hook, FP64.                         */
+/* Sec. V (simulation and cost calculation) notes that because every state  */
+/* of every step is computed explicitly, nonlinear effects such as contact  */
+/* or hard stops, and non-convex costs, can be put into the simulation as   */
+/* plain if/else.  This is one such hook, per state i with bounds           */
+/* lo_i <= hi_i and weight rho_i >= 0.  After each update                   */
+/*   x_{k+1} = A_d x_k + B_d u_k + w_d                                      */
+/* and for every state i, in this order:                                    */
+/*   d_i = max(0, lo_i - x_i, x_i - hi_i)   distance outside the box        */
+/*   mode bit 1 (value 2): J += rho_i d_i^2  (hinge penalty, soft limit)     */
+/*   mode bit 0 (value 1): x_i = min(max(x_i, lo_i), hi_i)  (hard stop)      */
+/* then the stage cost of the (stopped) state and u_k' R u_k as orc_cost    */
+/* conv 0.  The stopped state is the one the next step starts from.  With   */
+/* mode 0 this is orc_cost conv 0.  traj, if given, receives x_0..x_T.      */
+/* ------------------------------------------------------------------------ */
+ORC_EXPORT double orc_cost_box(const double* A, const double* B, const double* Q,
+                               const double* R, const double* w, const double* x0,
+                               const double* g, const double* U, int n, int m, int T, int p,
+                               const double* lo, const double* hi, const double* rho, int mode,
+                               double* traj) {
+    double* uexp = (double*)malloc(sizeof(double) * (size_t)T * (size_t)m);
+    double* x = (double*)malloc(sizeof(double) * (size_t)n);
+    double* xn = (double*)malloc(sizeof(double) * (size_t)n);
+    double* e = (double*)malloc(sizeof(double) * (size_t)n);
+    expand_inputs(U, m, T, p, uexp);
+    memcpy(x, x0, sizeof(double) * (size_t)n);
+    if (traj) memcpy(traj, x0, sizeof(double) * (size_t)n);
+    double J = 0.0;
+    for (int k = 0; k < T; ++k) {
+        const double* u = uexp + (size_t)k * m;
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += A[i * n + j] * x[j];
+            for (int j = 0; j < m; ++j) s += B[i * m + j] * u[j];
+            if (w) s += w[i];
+            xn[i] = s;
+        }
+        double pen = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double d = 0.0;
+            if (xn[i] < lo[i]) d = lo[i] - xn[i];
+            if (xn[i] > hi[i]) d = xn[i] - hi[i];
+            if (mode & 2) pen += rho[i] * d * d;
+            if (mode & 1) {
+                if (xn[i] < lo[i]) xn[i] = lo[i];
+                if (xn[i] > hi[i]) xn[i] = hi[i];
+            }
+        }
+        for (int i = 0; i < n; ++i) e[i] = xn[i] - g[i];
+        J += quad_form(Q, e, n) + quad_form(R, u, m) + pen;
+        memcpy(x, xn, sizeof(double) * (size_t)n);
+        if (traj) memcpy(traj + (size_t)(k + 1) * n, x, sizeof(double) * (size_t)n);
+    }
+    free(uexp);
+    free(x);
+    free(xn);
+    free(e);
+    return J;
+}
+
+/* orc_cost_box for a whole SoA population (pop[q*P + c], FP32 knots).       */
+ORC_EXPORT void orc_cost_population_box(const double* A, const double* B, const double* Q,
+                                        const double* R, const double* w, const double* x0,
+                                        const double* g, const float* pop, int n, int m, int T,
+                                        int p, int P, const double* lo, const double* hi,
+                                        const double* rho, int mode, double* cost) {
+    int D = m * p;
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < P; ++c) {
+        double* U = (double*)malloc(sizeof(double) * (size_t)D);
+        for (int q = 0; q < D; ++q) U[q] = (double)pop[(size_t)q * P + c];
+        cost[c] = orc_cost_box(A, B, Q, R, w, x0, g, U, n, m, T, p, lo, hi, rho, mode, NULL);
         free(U);
     }
 }

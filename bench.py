@@ -471,8 +471,10 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                 "traffic": tr["dram_bytes_per_launch"] if tr else None}
     compare = None
     loop = None
+    box = None
     if wl.name in ("c1", "c2") and not condensed:
         loop = closed_loop_line(E, wl, A, B, 1 + rank, not args.no_cpu_baseline)
+        box = state_box_line(E, wl, A, B, 1 + rank)
     if wl.name in ("c3", "c5") and rank == 0:
         compare = compare_variant(E, wl.name)
     # per generation: breed, rollout, select (+ the refinement kernel after the first;
@@ -500,6 +502,7 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
         "cpu_baseline": cpu,
         **({"compare": compare} if compare else {}),
         **({"closed_loop": loop} if loop else {}),
+        **({"state_box": box} if box else {}),
     }
 
 
@@ -530,6 +533,36 @@ def closed_loop_line(E, wl, A, B, seed, with_oracle):
             rec["oracle_actual_cost"] = Jo
             rec["actual_cost_rel_diff"] = abs(r["actual_cost"] - Jo) / abs(Jo)
         out[f"generations_{G}"] = rec
+    return out
+
+
+def state_box_line(E, wl, A, B, seed, reps=5):
+    """The state-box hook (hard stop plus hinge penalty on every state) on
+    the workload itself: rollout kernel time (CUDA events) and host-timed
+    solve time with the hook against the same problem without it."""
+    lo = np.full(wl.n, -0.5, np.float32)
+    hi = np.full(wl.n, 0.5, np.float32)
+    rho = np.full(wl.n, 10.0, np.float32)
+    x0, g = wl.start_goal()
+    prob = E.Problem(A, B, wl.Q(), wl.R(), wl.bounds(), wl.T, wl.p, wl.P, seed=seed,
+                     elite=wl.E, sigma=wl.sigma)
+    out = {"box": "every state in [-0.5, 0.5], rho 10, stop and hinge penalty"}
+    for tag in ("plain", "hooked"):
+        if tag == "hooked":
+            prob.set_state_box(lo, hi, rho, clamp=True, penalty=True)
+        prob.reset()
+        prob.solve(x0, g, wl.G)  # graphs captured
+        ms = []
+        for _ in range(reps):
+            prob.reset()
+            t, _, c = _timed_solve(prob, x0, g, wl.G)
+            ms.append(t)
+        _, roll_us, _ = prob.time_generation(20)
+        out[f"rollout_us_{tag}"] = roll_us
+        out[f"ms_per_solve_{tag}"] = float(np.median(ms))
+        out[f"final_cost_{tag}"] = float(c)
+    out["rollout_time_ratio"] = out["rollout_us_hooked"] / out["rollout_us_plain"]
+    prob.close()
     return out
 
 

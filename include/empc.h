@@ -135,6 +135,32 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal,
  */
 empc_status empc_set_sigma(empc_handle h, float sigma);
 
+/* Flags of empc_set_state_box. */
+enum { EMPC_BOX_CLAMP = 1, EMPC_BOX_PENALTY = 2 };
+
+/*
+ * empc_set_state_box - a nonlinear hook inside every rollout (Sec. V,
+ * simulation and cost calculation: because each state of each step is
+ * simulated, hard stops and non-convex state costs can be written into the
+ * simulation as if/else).  Per state i, host FP32 arrays of n entries:
+ * lo [n] (NULL: -inf), hi [n] (NULL: +inf), rho [n] (NULL: 0).  After every
+ * update x_{k+1} = A_d x_k + B_d u_k, for each state, in this order:
+ *   d_i = max(0, lo_i - x_i, x_i - hi_i)   (distance outside the box)
+ *   EMPC_BOX_PENALTY:  J += rho_i d_i^2      (soft state limit)
+ *   EMPC_BOX_CLAMP:    x_i = min(max(x_i, lo_i), hi_i)   (hard stop)
+ * and the stage cost then sees the stopped state, from which the next step
+ * starts.  flags = 0 turns the hook off (the arrays are then ignored).  It
+ * applies to every later empc_solve, empc_solve_device, empc_evaluate and
+ * empc_closed_loop call; empc_closed_loop also stops its plant at the box
+ * when EMPC_BOX_CLAMP is set.  Copies the arrays before returning.
+ * EMPC_EINVAL unless lo_i <= hi_i, lo_i < +inf, hi_i > -inf and rho_i is
+ * finite and >= 0 (NaN fails), or on unknown flag bits; EMPC_EUNSUPPORTED
+ * with a non-zero flag for BF16 precision, the condensed evaluator or
+ * refinement (none of them simulates the states one by one).
+ */
+empc_status empc_set_state_box(empc_handle h, const float* lo, const float* hi,
+                               const float* rho, int flags);
+
 /*
  * empc_closed_loop - receding-horizon control of a plant (Sec. III-A: solve,
  * apply only the first input, solve again from the new state; Sec. V: EMPC
@@ -152,7 +178,9 @@ empc_status empc_set_sigma(empc_handle h, float sigma);
  * actual_cost (Eq. actual_cost) = sum_k (x_goal - x_k)' Q (x_goal - x_k) +
  * u_k' R u_k over the applied steps plus the state term of the final state
  * x_steps; optional x_traj [(steps+1)*n], u_traj [steps*m] and the mean
- * wall time per step in ms (solve plus plant update).  Errors as empc_solve;
+ * wall time per step in ms (solve plus plant update).  With an
+ * EMPC_BOX_CLAMP state box (empc_set_state_box) the plant state is stopped
+ * at the box after each update.  Errors as empc_solve;
  * EMPC_ENONFINITE if the plant state diverges.
  */
 empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, const double* x0,

@@ -22,6 +22,7 @@ EMPC_ENONFINITE, EMPC_ESTATE, EMPC_EUNSUPPORTED = 5, 6, 7
 EMPC_FP32, EMPC_BF16 = 0, 1
 EMPC_GATE_PER_INPUT, EMPC_GATE_PER_KNOT, EMPC_GATE_ALWAYS = 0, 1, 2
 EMPC_EVAL_ROLLOUT, EMPC_EVAL_CONDENSED = 0, 1
+EMPC_BOX_CLAMP, EMPC_BOX_PENALTY = 1, 2
 
 _STATUS = {0: "EMPC_OK", 1: "EMPC_EINVAL", 2: "EMPC_ENOMEM", 3: "EMPC_ECUDA",
            4: "EMPC_ETIMEOUT", 5: "EMPC_ENONFINITE", 6: "EMPC_ESTATE",
@@ -94,6 +95,7 @@ _SIGNATURES = {
     "empc_closed_loop": (_i, [_h, _dp, _dp, _dp, _dp, _i, _i, ctypes.c_double, ctypes.c_double,
                               _dp, _dp, _dp, _dp]),
     "empc_set_sigma": (_i, [_h, ctypes.c_float]),
+    "empc_set_state_box": (_i, [_h, _fp, _fp, _fp, _i]),
     "empc_measure_fp32_peak": (_i, [_dp]),
     "empc_evaluate_noalloc": (_i, [_dp, _dp, _dp, _dp, _i, _i, _i, _i, _vp, _vp, _vp, _i,
                                   _vp, _vp]),
@@ -263,6 +265,20 @@ class Problem:
 
     def set_sigma(self, sigma):
         check(_lib.empc_set_sigma(self.handle, float(sigma)), self.handle)
+
+    def set_state_box(self, lo=None, hi=None, rho=None, clamp=False, penalty=False):
+        """The state-box hook inside every rollout: per-state bounds lo, hi
+        and weight rho (None: -inf, +inf, 0); `penalty` adds rho d^2 for the
+        distance d outside the box after each update, `clamp` stops the state
+        at the box.  Both False turn the hook off."""
+        flags = (EMPC_BOX_CLAMP if clamp else 0) | (EMPC_BOX_PENALTY if penalty else 0)
+        arrs = [None if v is None else np.ascontiguousarray(v, dtype=np.float32)
+                for v in (lo, hi, rho)]
+        for v in arrs:
+            if v is not None and v.shape != (self.n,):
+                raise ValueError(f"state box arrays need shape ({self.n},)")
+        ptrs = [None if v is None else v.ctypes.data_as(_fp) for v in arrs]
+        check(_lib.empc_set_state_box(self.handle, *ptrs, flags), self.handle)
 
     def closed_loop(self, Ad, Bd, x0, x_goal, steps, generations, sigma_min=0.0,
                     sigma_dref=0.0):

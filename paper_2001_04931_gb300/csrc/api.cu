@@ -72,6 +72,10 @@ struct empc_problem_s {
     int grad_cands = 1, grad_wpc = 2;
     float* sigma_dev = nullptr;  // the mutation sigma the breeding kernel reads
     float sigma_now = 0.0f;      // host copy being transferred to sigma_dev
+    // state-box hook: [3][n] lo, hi, rho on the device and its host copy
+    float* box = nullptr;
+    std::vector<float> box_h;
+    int box_mode = 0;
     // diag Q and diag R in FP64 (closed-loop actual cost)
     std::vector<double> qd_h, rd_h;
     // condensed evaluator: J(U) = U'HU + g'U + c0 (H padded to Dp x Dp)
@@ -128,6 +132,8 @@ RolloutArgs base_args(empc_handle h) {
     a.gen = h->gen;
     a.sigma = h->cfg.sigma;
     a.sigma_dev = h->sigma_dev;
+    a.box = h->box;
+    a.box_mode = h->box_mode;
     a.pc256 = h->cfg.p_cross_256;
     a.pm256 = h->cfg.p_mutate_256;
     a.gate = h->cfg.gate;
@@ -429,7 +435,7 @@ void free_handle(empc_handle h) {
     void* bufs[] = {h->D_, h->BT, h->qdiag, h->rdiag, h->gram, h->umin, h->umax, h->x0,
                     h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
                     h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
-                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev};
+                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev, h->box};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->stage) cudaFreeHost(h->stage);
@@ -775,6 +781,44 @@ empc_status empc_set_sigma(empc_handle h, float sigma) {
     return EMPC_OK;
 }
 
+empc_status empc_set_state_box(empc_handle h, const float* lo, const float* hi,
+                               const float* rho, int flags) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (flags & ~(EMPC_BOX_CLAMP | EMPC_BOX_PENALTY))
+        return fail(h, EMPC_EINVAL, "unknown state-box flags");
+    if (flags && (h->cfg.precision != EMPC_FP32 || h->cfg.evaluator != EMPC_EVAL_ROLLOUT ||
+                  h->cfg.refine_steps > 0))
+        return fail(h, EMPC_EUNSUPPORTED,
+                    "the state-box hook needs the FP32 rollout evaluator without refinement");
+    const int n = h->n;
+    std::vector<float> t(3 * (size_t)n);
+    if (flags) {
+        for (int i = 0; i < n; ++i) {
+            const float l = lo ? lo[i] : -INFINITY, u = hi ? hi[i] : INFINITY;
+            const float r = rho ? rho[i] : 0.0f;
+            if (!(l <= u) || l == INFINITY || u == -INFINITY)
+                return fail(h, EMPC_EINVAL, "state box needs lo <= hi, lo < +inf, hi > -inf");
+            if (!(r >= 0.0f) || !std::isfinite(r))
+                return fail(h, EMPC_EINVAL, "state box needs finite rho >= 0");
+            t[i] = l;
+            t[n + i] = u;
+            t[2 * n + i] = r;
+        }
+        if (!h->box) EMPC_CUDA(h, dev_alloc(&h->box, 3 * (size_t)n));
+        EMPC_CUDA(h, cudaMemcpyAsync(h->box, t.data(), sizeof(float) * t.size(),
+                                     cudaMemcpyHostToDevice, h->stream));
+        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    h->box_h = t;
+    if (flags != h->box_mode) {  // the captured generations carry the mode
+        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+        h->box_mode = flags;
+    }
+    return EMPC_OK;
+}
+
 empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, const double* x0,
                              const double* x_goal, int steps, int generations, double sigma_min,
                              double sigma_dref, double* x_traj, double* u_traj,
@@ -824,6 +868,8 @@ empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, 
             double v = 0.0;
             for (int c = 0; c < n; ++c) v += Ad[(size_t)r * n + c] * x[c];
             for (int c = 0; c < m; ++c) v += Bd[(size_t)r * m + c] * u[c];
+            if (h->box_mode & EMPC_BOX_CLAMP)  // the plant meets the same hard stop
+                v = std::min(std::max(v, (double)h->box_h[r]), (double)h->box_h[n + r]);
             xn[r] = v;
         }
         x.swap(xn);

@@ -44,6 +44,11 @@ struct RolloutArgs {
     float sigma;
     const float* sigma_dev;  // if set, the mutation sigma is read here (set per solve)
     int pc256, pm256, gate;
+    // state-box hook (Sec. V: hard stops and non-convex state costs inside the
+    // simulation): [3][n] lo, hi, rho on the device, read when box_mode != 0;
+    // box_mode bit 0 stops the state at [lo, hi], bit 1 adds rho d^2
+    const float* box;
+    int box_mode;
     int cand_begin;  // first candidate this launch covers (later ones up to P)
     int pdl;         // launch with programmatic stream serialization
     int* status;     // bit 1 (value 2): a bounded device wait gave up (may be null)

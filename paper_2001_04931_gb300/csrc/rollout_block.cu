@@ -20,7 +20,7 @@ namespace empc {
 namespace {
 
 struct BlockLayout {
-    int xs, off_x, off_u, off_bt, off_k, off_par, total;
+    int xs, off_x, off_u, off_bt, off_k, off_par, off_box, total;
     __host__ __device__ BlockLayout(int nx, int ptile, int m, int p, int T) {
         xs = round_up(ptile, 4);
         off_x = 0;
@@ -28,7 +28,8 @@ struct BlockLayout {
         off_bt = off_u + m * p * xs;
         off_k = round_up(off_bt + m * nx, 4);
         off_par = off_k + 4 * T;
-        total = off_par + 2 * xs;
+        off_box = off_par + 2 * xs;
+        total = off_box + 3 * nx;
     }
 };
 
@@ -61,13 +62,15 @@ __global__ void rollout_block_kernel(const RolloutArgs a) {
         BTs[i] = row < n ? a.BT[col * n + row] : 0.0f;
     }
     for (int k = tid; k < a.T; k += blockDim.x) ks[k] = a.ktab[k];
+    float* Bx = smem + L.off_box;
+    if (a.box_mode) stage_box(a, Bx, NX, tid, blockDim.x);
     float d[R][NX], qd[R], gl[R], xo[R][C], jsum[C];
     load_rows<NX, R, C>(a, rg * R, d, qd, gl, xo);
     pdl_wait_primary();
     const uint32_t gen = a.gen ? *a.gen : 0u;
     fill_knots<false>(a, Us, xs, par, c0, ptile, gen, tid, blockDim.x);  // ends with a barrier
     horizon_loop<NX, R, C, false>(a, d, X, NX, xs, BTs, NX, Us, ks, rg * R, cg * C, xo, qd, gl,
-                                  jsum);
+                                  jsum, a.box_mode ? Bx : nullptr);
 
     // reduce the row groups in order, then add the input cost
     float* Jred = X;  // every state read is done (barrier at the end of the loop)
@@ -192,7 +195,8 @@ size_t rollout_smem_bytes(const TileShape& s, int n, int m, int p, int T) {
         const int cpw = (32 / nrg) * s.cands;
         const int xsw = round_up(cpw, 4);
         const int per_warp = round_up(2 * xr * xsw + m * p * xsw + 2 * xsw, 4);
-        const int head = round_up(m * xr, 4) + 4 * T + round_up(n * (s.nx + 2), 4);
+        const int head = round_up(m * xr, 4) + 4 * T + round_up(n * (s.nx + 2), 4) +
+                         round_up(3 * xr, 4);
         return sizeof(float) * (size_t)(head + s.groups * per_warp);
     }
     const BlockLayout L(s.nx, s.groups * s.cands, m, p, T);

@@ -402,6 +402,31 @@ __device__ __forceinline__ float input_cost_part(const Args& a, const float* Us,
     return Ju;
 }
 
+// The state-box hook for one state (Sec. V: with every state of every step
+// simulated, hard stops and non-convex state costs go into the simulation as
+// plain if/else).  bx is [3][ld] (lo, hi, rho; rows past n hold -inf, +inf,
+// 0).  With mode bit 1 adds rho d^2 to j, d = max(0, lo - x, x - hi) the
+// distance outside the box; with mode bit 0 returns x stopped at the box.
+__device__ __forceinline__ float box_hook(const float* bx, int ld, int row, int mode, float x,
+                                          float& j) {
+    const float lo = bx[row], hi = bx[ld + row];
+    if (mode & 2) {
+        const float d = fmaxf(fmaxf(lo - x, x - hi), 0.0f);
+        j = fmaf(bx[2 * ld + row] * d, d, j);
+    }
+    return (mode & 1) ? fminf(fmaxf(x, lo), hi) : x;
+}
+
+// Stage the box of rows 0 .. ld-1 into shared memory (padding rows never bind).
+__device__ __forceinline__ void stage_box(const RolloutArgs& a, float* bx, int ld, int t,
+                                          int nt) {
+    for (int i = t; i < 3 * ld; i += nt) {
+        const int which = i / ld, row = i - which * ld;
+        const float pad = which == 0 ? -INFINITY : which == 1 ? INFINITY : 0.0f;
+        bx[i] = row < a.n ? a.box[which * a.n + row] : pad;
+    }
+}
+
 __device__ __forceinline__ float finite_or_inf(float v) {
     return (v == v) ? v : __int_as_float(0x7f800000);
 }
@@ -421,7 +446,7 @@ __device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (
                                              int ldb, const float* Us, const KnotStep* ks,
                                              int row0, int col0, float (&xo)[R][C],
                                              const float (&qd)[R], const float (&gl)[R],
-                                             float (&jsum)[C]) {
+                                             float (&jsum)[C], const float* bx = nullptr) {
     float bua[R][C], bub[R][C];
     int seg = -1;
     float jtot[C], jblk[C];
@@ -462,6 +487,7 @@ __device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 xn[c] = xo[r][c] + acc[r][c];
+                if (bx) xn[c] = box_hook(bx, xrows, row0 + r, a.box_mode, xn[c], jblk[c]);
                 xo[r][c] = xn[c];
                 const float e = xn[c] - gl[r];
                 jblk[c] = fmaf(qd[r] * e, e, jblk[c]);

@@ -23,15 +23,15 @@ __host__ __device__ constexpr int nrg_of(int nx) {
 
 // The horizon loop of rollout_common.cuh's horizon_loop on the
 // pair-interleaved state tile, with paired FMAs and two partial sums per
-// output (state_product_pairs).
-template <int NX, int R, int C>
+// output (state_product_pairs).  BOX compiles in the state-box hook (bx).
+template <int NX, int R, int C, bool BOX>
 __device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
                                                    const float2 (&d2)[R][NX / 2], float* X,
                                                    int xrows, int xs, const float* BTs, int ldb,
                                                    const float* Us, const KnotStep* ks,
                                                    int row0, int col0, float (&xo)[R][C],
                                                    const float (&qd)[R], const float (&gl)[R],
-                                                   float (&jsum)[C]) {
+                                                   float (&jsum)[C], const float* bx) {
     float bua[R][C], bub[R][C];
     int seg = -1;
     float jtot[C], jblk[C];
@@ -72,7 +72,8 @@ __device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const float sum = acc[r][c].x + acc[r][c].y;
-                const float xn = xo[r][c] + sum;
+                float xn = xo[r][c] + sum;
+                if constexpr (BOX) xn = box_hook(bx, xrows, row0 + r, a.box_mode, xn, jblk[c]);
                 xo[r][c] = xn;
                 const float e = xn - gl[r];
                 jblk[c] = fmaf(qd[r] * e, e, jblk[c]);
@@ -106,13 +107,15 @@ __host__ __device__ constexpr int warp_slice_floats(int D) {
 // problem `a` and writes their costs.  W is the warp's shared-memory slice;
 // BTs ([m][XR], rows past n zero) and ks (knot table) are staged by the CTA,
 // and so is D when Ds is given ([n][ds] with ds >= NX, columns past n zero;
-// otherwise the rows are read from global memory).
+// otherwise the rows are read from global memory).  bx, if given, is the
+// state box staged as [3][XR] (stage_box) and turns on the hook.
 // Reads the population, the elites and the generation counter only after
 // pdl_wait_primary(); COHERENT reads them through L2 (persistent kernels).
 template <int NX, int C, bool COHERENT = false>
 __device__ __forceinline__ void warp_tile(const RolloutArgs& a, int c0, float* W,
                                           const float* BTs, const KnotStep* ks,
-                                          const float* Ds = nullptr, int ds = 0) {
+                                          const float* Ds = nullptr, int ds = 0,
+                                          const float* bx = nullptr) {
     constexpr int NRG = nrg_of(NX);
     constexpr int R = (NX + NRG - 1) / NRG;
     constexpr int XR = NRG * R;
@@ -161,8 +164,12 @@ __device__ __forceinline__ void warp_tile(const RolloutArgs& a, int c0, float* W
     pdl_wait_primary();
     const uint32_t gen = a.gen ? *(volatile const uint32_t*)a.gen : 0u;
     fill_knots<true, COHERENT>(a, Us, XS, par, c0, CPW, gen, lane, 32);  // ends with a warp barrier
-    horizon_loop_pairs<NX, R, C>(a, d2, X, XR, XS, BTs, XR, Us, ks, rg * R, cgl * C, xo, qd, gl,
-                                 jsum);
+    if (bx)
+        horizon_loop_pairs<NX, R, C, true>(a, d2, X, XR, XS, BTs, XR, Us, ks, rg * R, cgl * C,
+                                           xo, qd, gl, jsum, bx);
+    else
+        horizon_loop_pairs<NX, R, C, false>(a, d2, X, XR, XS, BTs, XR, Us, ks, rg * R, cgl * C,
+                                            xo, qd, gl, jsum, bx);
 
     // each lane adds the input cost of inputs rg, rg + NRG, ...; then a
     // butterfly over the group's NRG lanes

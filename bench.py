@@ -446,6 +446,15 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                 "launch_us": roll_us, "breed_us": breed_us, "select_us": sel_us,
                 "traffic": (lambda t: t["dram_bytes_per_launch"] if t else None)(
                     traffic_record("c5"))}
+        # the FP32 work beside the MMA, against the FP32 pipe: per candidate
+        # and step 3n for the stage cost (x - g, q e^2) and 3m for the input
+        # blend w0 U_a + w1 U_b
+        fp32_peak_tf, fp32_basis, _ = fp32_peak(E, clocks, local_rank)
+        ep_flops = wl.P * wl.T * (3 * wl.n + 3 * wl.m)
+        ep_ach = ep_flops / (roll_us * 1e-6) / 1e12
+        roof["epilogue_fp32"] = {"flops_per_launch": ep_flops, "achieved": ep_ach,
+                                 "peak": fp32_peak_tf, "unit": "TFLOP/s",
+                                 "frac": ep_ach / fp32_peak_tf, "peak_basis": fp32_basis}
     elif condensed:
         peak, basis, measured = fp32_peak(E, clocks, local_rank)
         D = wl.m * wl.p

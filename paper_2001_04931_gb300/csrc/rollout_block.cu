@@ -69,8 +69,12 @@ __global__ void rollout_block_kernel(const RolloutArgs a) {
     pdl_wait_primary();
     const uint32_t gen = a.gen ? *a.gen : 0u;
     fill_knots<false>(a, Us, xs, par, c0, ptile, gen, tid, blockDim.x);  // ends with a barrier
-    horizon_loop<NX, R, C, false>(a, d, X, NX, xs, BTs, NX, Us, ks, rg * R, cg * C, xo, qd, gl,
-                                  jsum, a.box_mode ? Bx : nullptr);
+    if (a.box_mode)
+        horizon_loop<NX, R, C, false, true>(a, d, X, NX, xs, BTs, NX, Us, ks, rg * R, cg * C, xo,
+                                            qd, gl, jsum, Bx);
+    else
+        horizon_loop<NX, R, C, false>(a, d, X, NX, xs, BTs, NX, Us, ks, rg * R, cg * C, xo, qd,
+                                      gl, jsum);
 
     // reduce the row groups in order, then add the input cost
     float* Jred = X;  // every state read is done (barrier at the end of the loop)

@@ -439,8 +439,9 @@ namespace empc {
 // (columns col0 .. col0+C-1 of the state tile X[2][xrows][xs]).  D rows are
 // in registers; BU pairs are refreshed at knot-segment changes; the stage
 // cost is accumulated in 16-step blocks.  One barrier (warp or block) per
-// step separates the double-buffered state reads from the writes.
-template <int NX, int R, int C, bool WARP>
+// step separates the double-buffered state reads from the writes.  BOX
+// compiles in the state-box hook (bx).
+template <int NX, int R, int C, bool WARP, bool BOX = false>
 __device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (&d)[R][NX],
                                              float* X, int xrows, int xs, const float* BTs,
                                              int ldb, const float* Us, const KnotStep* ks,
@@ -487,7 +488,7 @@ __device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 xn[c] = xo[r][c] + acc[r][c];
-                if (bx) xn[c] = box_hook(bx, xrows, row0 + r, a.box_mode, xn[c], jblk[c]);
+                if constexpr (BOX) xn[c] = box_hook(bx, xrows, row0 + r, a.box_mode, xn[c], jblk[c]);
                 xo[r][c] = xn[c];
                 const float e = xn[c] - gl[r];
                 jblk[c] = fmaf(qd[r] * e, e, jblk[c]);

@@ -236,8 +236,10 @@ empc_status empc_evaluate_noalloc(const double* A, const double* B, const double
  * dev_grad [m*p][count] (same layout) and dev_cost [count]; either output
  * may be NULL, not both.  The forward pass keeps the state every ckpt_every
  * steps and the backward pass recomputes each segment from its checkpoint,
- * so memory is O(T/ckpt_every + ckpt_every) states per candidate.  FP32.
- * Needs n <= 64 (else EMPC_EUNSUPPORTED).  Asynchronous.  The paper's
+ * so memory is O(T/ckpt_every + ckpt_every) states per candidate.  FP32
+ * whatever cfg.precision is.  EMPC_EUNSUPPORTED for n > 64, while a state
+ * box is set (empc_set_state_box), or when the checkpoints do not fit in
+ * shared memory.  Asynchronous.  The paper's
  * optimizer is gradient-free; this is a library addition (with
  * cfg.refine_steps > 0 the elites of every generation take that many
  * projected-gradient steps U <- clip(U - eta dJ/dU) before the next one).

@@ -308,6 +308,50 @@ class Problem:
         check(_lib.empc_set_stream(self.handle, stream), self.handle)
 
 
+_COST_FN = None
+
+
+def _cost_function():
+    """The torch.autograd.Function behind rollout_cost (built on first use so
+    that importing this module does not import torch)."""
+    global _COST_FN
+    if _COST_FN is None:
+        import torch
+
+        class RolloutCost(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, pop, x0, x_goal, problem):
+                cost = torch.empty(pop.shape[1], device=pop.device, dtype=torch.float32)
+                if ctx.needs_input_grad[0]:
+                    grad = torch.empty_like(pop)
+                    problem.grad(x0, x_goal, pop, grad, cost)  # costs and dJ/dU, one launch
+                    ctx.save_for_backward(grad)
+                else:
+                    problem.evaluate(x0, x_goal, pop, cost)
+                return cost
+
+            @staticmethod
+            def backward(ctx, grad_cost):
+                (grad,) = ctx.saved_tensors
+                return grad * grad_cost.unsqueeze(0), None, None, None
+
+        _COST_FN = RolloutCost
+    return _COST_FN
+
+
+def rollout_cost(problem, x0, x_goal, pop):
+    """Differentiable population cost: J [count] (FP32) of the knot vectors
+    pop [m*p, count] (contiguous CUDA float32, SoA like the population) from
+    x0 and x_goal (CUDA float32 [n]).  When pop requires grad, the forward
+    pass runs empc_grad, which returns the costs and the adjoint dJ/dU in one
+    launch, and the backward pass scales dJ/dU by the incoming gradient of J;
+    otherwise it runs empc_evaluate.  The library works on torch's current
+    stream (set_stream), so the results are ordered like any torch op."""
+    import torch
+    problem.set_stream(torch.cuda.current_stream().cuda_stream)
+    return _cost_function().apply(pop, x0, x_goal, problem)
+
+
 def _bcheck(status, batch):
     if status != EMPC_OK:
         msg = _lib.empc_batch_last_error(batch)

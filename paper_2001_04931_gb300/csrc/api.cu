@@ -70,6 +70,7 @@ struct empc_problem_s {
     int ce = 1;            // checkpoint interval
     float eta = 0.0f;      // refinement step
     int grad_cands = 1, grad_wpc = 2;
+    int grad_nx = 0;  // the adjoint kernel's state class (the warp family's, n <= 64)
     float* sigma_dev = nullptr;  // the mutation sigma the breeding kernel reads
     float sigma_now = 0.0f;      // host copy being transferred to sigma_dev
     // state-box hook: [3][n] lo, hi, rho on the device and its host copy
@@ -186,7 +187,7 @@ cudaError_t condensed_terms(empc_handle h, cudaStream_t st) {
     g.ld_grad = 1;
     g.cost = h->c0;
     g.steps = 0;
-    return empc::launch_grad(g, h->shape.nx, h->grad_cands, h->grad_wpc, st);
+    return empc::launch_grad(g, h->grad_nx, h->grad_cands, h->grad_wpc, st);
 }
 
 // One generation into pop[parity^1], then elite selection.  Cold: draw every
@@ -218,7 +219,7 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
         g.steps = h->cfg.refine_steps;
         if ((e = cudaEventRecord(h->ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0)) != cudaSuccess) return e;
-        e = empc::launch_grad(g, h->shape.nx, h->grad_cands, h->grad_wpc, h->aux_stream);
+        e = empc::launch_grad(g, h->grad_nx, h->grad_cands, h->grad_wpc, h->aux_stream);
         if (e != cudaSuccess) return e;
         if ((e = cudaEventRecord(h->ev_join, h->aux_stream)) != cudaSuccess) return e;
     }
@@ -720,8 +721,9 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
         // whose shared memory fits
         h->grad_cands = 1;
         h->grad_wpc = 0;
+        h->grad_nx = empc::warp_class_nx(n);
         for (int wpc : {4, 2, 1}) {
-            const size_t need = empc::grad_smem_bytes(h->shape.nx, empc::warp_nrg(h->shape.nx), 1,
+            const size_t need = empc::grad_smem_bytes(h->grad_nx, empc::warp_nrg(h->grad_nx), 1,
                                                       wpc, n, m, knots, horizon, h->ce);
             if (need <= 227u * 1024u) {
                 h->grad_wpc = wpc;
@@ -929,6 +931,10 @@ empc_status empc_grad(empc_handle h, const float* dev_x0, const float* dev_goal,
         return fail(h, EMPC_EINVAL, "NULL device pointer");
     if (count < 0) return fail(h, EMPC_EINVAL, "count must be >= 0");
     if (h->n > 64) return fail(h, EMPC_EUNSUPPORTED, "the adjoint kernel needs n <= 64");
+    if (h->box_mode)
+        return fail(h, EMPC_EUNSUPPORTED, "the adjoint follows the dynamics without the state box");
+    if (h->grad_wpc <= 0)
+        return fail(h, EMPC_EUNSUPPORTED, "adjoint checkpoints do not fit in shared memory");
     if (count == 0) return EMPC_OK;
     empc::GradArgs g = grad_args(h);
     g.x0 = dev_x0;
@@ -940,7 +946,7 @@ empc_status empc_grad(empc_handle h, const float* dev_x0, const float* dev_goal,
     g.ld_grad = count;
     g.cost = dev_cost;
     g.steps = 0;
-    EMPC_CUDA(h, empc::launch_grad(g, h->shape.nx, h->grad_cands, h->grad_wpc, h->stream));
+    EMPC_CUDA(h, empc::launch_grad(g, h->grad_nx, h->grad_cands, h->grad_wpc, h->stream));
     return EMPC_OK;
 }
 

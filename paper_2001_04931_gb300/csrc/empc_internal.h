@@ -156,6 +156,8 @@ cudaError_t launch_rollout_warp(const RolloutArgs& a, const TileShape& s, cudaSt
 int block_max_threads(const TileShape& s);
 int warp_max_threads(const TileShape& s);
 int warp_nrg(int nx);
+// The warp family's compiled state class for n <= 64 (4 .. 64), else 0.
+int warp_class_nx(int n);
 
 // Elite selection: E lowest of P costs by (cost, index), NaN as +inf.
 // Writes elite_idx[E], elite_cost[E], best_knots[m p] and increments *gen.

@@ -156,6 +156,11 @@ static int compiled_nx(int n) {
     return 0;
 }
 
+int warp_class_nx(int n) {
+    const int nx = compiled_nx(n);
+    return nx <= 64 ? nx : 0;
+}
+
 int rollout_shapes(int n, TileShape* out, int cap) {
     const int nx = compiled_nx(n);
     int k = 0;

@@ -172,8 +172,10 @@ int rollout_shapes(int n, TileShape* out, int cap) {
     if (nx <= 64) {  // warp-synchronous family
         const int nrg = warp_nrg(nx);
         const int rows = (nx + nrg - 1) / nrg;
+        // 7 warps a CTA: where 8 leave SMs idle (4096 candidates of 2 per
+        // lane fill 128 CTAs of 8 warps), 147 CTAs of 7 use nearly all 152
         for (int cands : {2, 1, 4})
-            for (int wpc : {1, 2, 4, 8}) push(TileShape{1, nx, rows, cands, wpc});
+            for (int wpc : {1, 2, 4, 8, 7}) push(TileShape{1, nx, rows, cands, wpc});
     }
     const int rows = nx == 128 ? 1 : 2;
     const int nrg = (n + rows - 1) / rows;

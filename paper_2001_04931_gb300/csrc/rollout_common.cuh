@@ -229,6 +229,7 @@ __device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad
         uint32_t gate_blk = 0xFFFFFFFFu;
         float z[4];
         bool have_z = false;
+        const float sg = noise_sigma(a);  // one read of the (device) sigma per quad
         int i = q0 / a.p, j = q0 - i * a.p;  // input and knot of q0, advanced below
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -253,7 +254,7 @@ __device__ __forceinline__ void breed_quad(const RolloutArgs& a, int c, int quad
                         gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
                         have_z = true;
                     }
-                    val = __fmaf_rn(noise_sigma(a), z[w], mate[w]);
+                    val = __fmaf_rn(sg, z[w], mate[w]);
                 }
                 v[w] = clamp_to(val, a.umin[i], a.umax[i]);
             }
@@ -292,6 +293,7 @@ __device__ __forceinline__ void breed_hex_warm(const RolloutArgs& a, int c, int 
         }
         float z[4];
         bool have_z = false;
+        const float sg = noise_sigma(a);
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int q = q0 + w;
@@ -315,7 +317,7 @@ __device__ __forceinline__ void breed_hex_warm(const RolloutArgs& a, int c, int 
                     gauss_pair(nz.w[2], nz.w[3], &z[2], &z[3]);
                     have_z = true;
                 }
-                val = __fmaf_rn(noise_sigma(a), z[w], mate[w]);
+                val = __fmaf_rn(sg, z[w], mate[w]);
             }
             emit(q, clamp_to(val, a.umin[i], a.umax[i]));
         }

@@ -402,7 +402,9 @@ def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations, sigma_min=0.0, s
     sigma_dref)) with sigma0 the EMPC object's (FP32) sigma and the norm
     summed in index order, rounded to FP32.  Actual cost (Eq. actual_cost):
     the stage costs (goal - x_k)' Q (goal - x_k) + u_k' R u_k over the applied
-    steps plus the state term of the final state.  With the EMPC object's
+    steps plus the state term of the final state.  The model's constant
+    disturbance w_d (Eq. first_order_integration), if it has one, acts on the
+    plant too: x_{k+1} = Ad x_k + Bd u_k + w_d.  With the EMPC object's
     StateBox set to clamp, the plant is stopped at the same box after every
     step.  Returns (x [(steps+1), n], u [steps, m], actual cost, sigmas
     [steps])."""
@@ -424,6 +426,8 @@ def closed_loop(ga, Ad, Bd, Q, R, x0, goal, steps, generations, sigma_min=0.0, s
         e = goal - x
         total += e @ Q @ e + u @ R @ u
         x = Ad @ x + Bd @ u
+        if ga.model.w is not None:
+            x = x + ga.model.w
         if ga.box is not None:
             x = ga.box.stop(x)
         xs.append(x.copy())

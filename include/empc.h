@@ -135,6 +135,17 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal,
  */
 empc_status empc_set_sigma(empc_handle h, float sigma);
 
+/*
+ * empc_set_disturbance - the constant disturbance w_d of Eq.
+ * first_order_integration, x_{k+1} = A_d x_k + B_d u_k + w_d: host FP64
+ * w_d [n], rounded to FP32 for the rollouts; NULL or all zeros removes it.
+ * It applies to every later solve, evaluation and gradient (and so to the
+ * condensed evaluator's terms), and empc_closed_loop adds it to its plant.
+ * Copies the array before returning.  EMPC_EINVAL for a non-finite entry;
+ * EMPC_EUNSUPPORTED for a non-zero w_d with BF16 precision.
+ */
+empc_status empc_set_disturbance(empc_handle h, const double* w_d);
+
 /* Flags of empc_set_state_box. */
 enum { EMPC_BOX_CLAMP = 1, EMPC_BOX_PENALTY = 2 };
 
@@ -178,7 +189,8 @@ empc_status empc_set_state_box(empc_handle h, const float* lo, const float* hi,
  * actual_cost (Eq. actual_cost) = sum_k (x_goal - x_k)' Q (x_goal - x_k) +
  * u_k' R u_k over the applied steps plus the state term of the final state
  * x_steps; optional x_traj [(steps+1)*n], u_traj [steps*m] and the mean
- * wall time per step in ms (solve plus plant update).  With an
+ * wall time per step in ms (solve plus plant update).  A disturbance set by
+ * empc_set_disturbance is added to the plant update.  With an
  * EMPC_BOX_CLAMP state box (empc_set_state_box) the plant state is stopped
  * at the box after each update.  Errors as empc_solve;
  * EMPC_ENONFINITE if the plant state diverges.

@@ -96,6 +96,7 @@ _SIGNATURES = {
                               _dp, _dp, _dp, _dp]),
     "empc_set_sigma": (_i, [_h, ctypes.c_float]),
     "empc_set_state_box": (_i, [_h, _fp, _fp, _fp, _i]),
+    "empc_set_disturbance": (_i, [_h, _dp]),
     "empc_measure_fp32_peak": (_i, [_dp]),
     "empc_evaluate_noalloc": (_i, [_dp, _dp, _dp, _dp, _i, _i, _i, _i, _vp, _vp, _vp, _i,
                                   _vp, _vp]),
@@ -265,6 +266,17 @@ class Problem:
 
     def set_sigma(self, sigma):
         check(_lib.empc_set_sigma(self.handle, float(sigma)), self.handle)
+
+    def set_disturbance(self, w_d=None):
+        """The constant disturbance w_d [n] of x_{k+1} = A_d x_k + B_d u_k +
+        w_d (None or zeros: none)."""
+        if w_d is None:
+            check(_lib.empc_set_disturbance(self.handle, None), self.handle)
+            return
+        w = _d(w_d)
+        if w.shape != (self.n,):
+            raise ValueError(f"w_d needs shape ({self.n},)")
+        check(_lib.empc_set_disturbance(self.handle, _ptr(w)), self.handle)
 
     def set_state_box(self, lo=None, hi=None, rho=None, clamp=False, penalty=False):
         """The state-box hook inside every rollout: per-state bounds lo, hi

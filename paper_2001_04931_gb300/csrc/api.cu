@@ -77,6 +77,10 @@ struct empc_problem_s {
     float* box = nullptr;
     std::vector<float> box_h;
     int box_mode = 0;
+    // constant disturbance w_d: [n] FP32 on the device, FP64 host copy
+    float* wd_dev = nullptr;
+    std::vector<double> wd_h;
+    bool has_wd = false;
     // diag Q and diag R in FP64 (closed-loop actual cost)
     std::vector<double> qd_h, rd_h;
     // condensed evaluator: J(U) = U'HU + g'U + c0 (H padded to Dp x Dp)
@@ -135,6 +139,7 @@ RolloutArgs base_args(empc_handle h) {
     a.sigma_dev = h->sigma_dev;
     a.box = h->box;
     a.box_mode = h->box_mode;
+    a.wd = h->has_wd ? h->wd_dev : nullptr;
     a.pc256 = h->cfg.p_cross_256;
     a.pm256 = h->cfg.p_mutate_256;
     a.gate = h->cfg.gate;
@@ -152,6 +157,7 @@ empc::GradArgs grad_args(empc_handle h) {
     g.ktab = h->ktab;
     g.x0 = h->x0;
     g.goal = h->goal;
+    g.wd = h->has_wd ? h->wd_dev : nullptr;
     g.umin = h->umin;
     g.umax = h->umax;
     g.n = h->n;
@@ -436,7 +442,8 @@ void free_handle(empc_handle h) {
     void* bufs[] = {h->D_, h->BT, h->qdiag, h->rdiag, h->gram, h->umin, h->umax, h->x0,
                     h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
                     h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
-                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev, h->box};
+                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev, h->box,
+                    h->wd_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->stage) cudaFreeHost(h->stage);
@@ -821,6 +828,36 @@ empc_status empc_set_state_box(empc_handle h, const float* lo, const float* hi,
     return EMPC_OK;
 }
 
+empc_status empc_set_disturbance(empc_handle h, const double* w_d) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    const int n = h->n;
+    bool nonzero = false;
+    if (w_d) {
+        if (!empc::all_finite(w_d, (size_t)n)) return fail(h, EMPC_EINVAL, "non-finite w_d");
+        for (int i = 0; i < n; ++i) nonzero = nonzero || w_d[i] != 0.0;
+    }
+    if (nonzero && h->cfg.precision != EMPC_FP32)
+        return fail(h, EMPC_EUNSUPPORTED, "the disturbance needs the FP32 rollout");
+    if (nonzero) {
+        std::vector<float> t(n);
+        for (int i = 0; i < n; ++i) t[i] = (float)w_d[i];
+        if (!h->wd_dev) EMPC_CUDA(h, dev_alloc(&h->wd_dev, (size_t)n));
+        EMPC_CUDA(h, cudaMemcpyAsync(h->wd_dev, t.data(), sizeof(float) * n,
+                                     cudaMemcpyHostToDevice, h->stream));
+        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+        h->wd_h.assign(w_d, w_d + n);
+    } else {
+        h->wd_h.clear();
+    }
+    if (nonzero != h->has_wd) {  // the captured generations carry the pointer
+        EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+        h->has_wd = nonzero;
+    }
+    return EMPC_OK;
+}
+
 empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, const double* x0,
                              const double* x_goal, int steps, int generations, double sigma_min,
                              double sigma_dref, double* x_traj, double* u_traj,
@@ -870,6 +907,7 @@ empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, 
             double v = 0.0;
             for (int c = 0; c < n; ++c) v += Ad[(size_t)r * n + c] * x[c];
             for (int c = 0; c < m; ++c) v += Bd[(size_t)r * m + c] * u[c];
+            if (h->has_wd) v += h->wd_h[r];  // the model's disturbance acts on the plant
             if (h->box_mode & EMPC_BOX_CLAMP)  // the plant meets the same hard stop
                 v = std::min(std::max(v, (double)h->box_h[r]), (double)h->box_h[n + r]);
             xn[r] = v;

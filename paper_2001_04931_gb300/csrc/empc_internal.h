@@ -49,6 +49,9 @@ struct RolloutArgs {
     // box_mode bit 0 stops the state at [lo, hi], bit 1 adds rho d^2
     const float* box;
     int box_mode;
+    // constant disturbance w_d of Eq. first_order_integration: [n] on the
+    // device, or null (zero)
+    const float* wd;
     int cand_begin;  // first candidate this launch covers (later ones up to P)
     int pdl;         // launch with programmatic stream serialization
     int* status;     // bit 1 (value 2): a bounded device wait gave up (may be null)
@@ -97,6 +100,7 @@ struct GradArgs {
     int ce;               // checkpoint interval
     int steps;            // projected-gradient steps (0: gradient only)
     float eta;            // step size
+    const float* wd;      // constant disturbance w_d [n], or null (zero)
 };
 
 cudaError_t launch_grad(const GradArgs& a, int nx, int cands, int wpc, cudaStream_t st);

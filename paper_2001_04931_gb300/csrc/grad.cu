@@ -89,12 +89,14 @@ __device__ __forceinline__ void knot_pair(const GradArgs& a, const float* BTs, i
     seg = st.idx1;
 }
 
-// One forward step from state tile Xin to Xout (own rows): x + D x + B u_k.
+// One forward step from state tile Xin to Xout (own rows): x + D x + B u_k,
+// then + w_d (wdr: this thread's rows of the disturbance, zero without one).
 template <int NX, int R, int C>
 __device__ __forceinline__ void fwd_step(const float (&d)[R][NX], const float* Xin,
                                          float* Xout, int xs, int row0, int col0,
                                          const KnotStep& st, const float (&bua)[R][C],
-                                         const float (&bub)[R][C], float (&xo)[R][C]) {
+                                         const float (&bub)[R][C], const float (&wdr)[R],
+                                         float (&xo)[R][C]) {
     float acc[R][C];
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -106,7 +108,7 @@ __device__ __forceinline__ void fwd_step(const float (&d)[R][NX], const float* X
         float xn[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            xn[c] = xo[r][c] + acc[r][c];
+            xn[c] = (xo[r][c] + acc[r][c]) + wdr[r];
             xo[r][c] = xn[c];
         }
         store_vec<C>(Xout + (row0 + r) * xs + col0, xn);
@@ -166,10 +168,11 @@ __global__ void grad_warp_kernel(const GradArgs a) {
     }
     __syncwarp();
 
-    float qd[R], gl[R], x0r[R];
+    float qd[R], gl[R], x0r[R], wdr[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
+        wdr[r] = (row < n && a.wd) ? a.wd[row] : 0.0f;
         qd[r] = row < n ? a.qdiag[row] : 0.0f;
         gl[r] = row < n ? a.goal[row] : 0.0f;
         x0r[r] = row < n ? a.x0[row] : 0.0f;
@@ -204,7 +207,7 @@ __global__ void grad_warp_kernel(const GradArgs a) {
             const KnotStep st = ks[k];
             knot_pair<R, C>(a, BTs, XR, Us, XS, row0, col0, st, seg, bua, bub);
             fwd_step<NX, R, C>(d, X + buf * XR * XS, X + (buf ^ 1) * XR * XS, XS, row0, col0,
-                               st, bua, bub, xo);
+                               st, bua, bub, wdr, xo);
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -277,7 +280,7 @@ __global__ void grad_warp_kernel(const GradArgs a) {
                 const KnotStep st = ks[k];
                 knot_pair<R, C>(a, BTs, XR, Us, XS, row0, col0, st, rseg, bua, bub);
                 const float* xin = (k == k0) ? CK + s * XR * XS : SB + (k - k0 - 1) * XR * XS;
-                fwd_step<NX, R, C>(d, xin, SB + (k - k0) * XR * XS, XS, row0, col0, st, bua, bub, xr);
+                fwd_step<NX, R, C>(d, xin, SB + (k - k0) * XR * XS, XS, row0, col0, st, bua, bub, wdr, xr);
                 __syncwarp();
             }
             // adjoint through the segment with D' rows

@@ -29,7 +29,7 @@ struct BlockLayout {
         off_k = round_up(off_bt + m * nx, 4);
         off_par = off_k + 4 * T;
         off_box = off_par + 2 * xs;
-        total = off_box + 3 * nx;
+        total = off_box + 4 * nx;
     }
 };
 
@@ -63,13 +63,14 @@ __global__ void rollout_block_kernel(const RolloutArgs a) {
     }
     for (int k = tid; k < a.T; k += blockDim.x) ks[k] = a.ktab[k];
     float* Bx = smem + L.off_box;
-    if (a.box_mode) stage_box(a, Bx, NX, tid, blockDim.x);
+    const bool hooks = has_hooks(a);
+    if (hooks) stage_box(a, Bx, NX, tid, blockDim.x);
     float d[R][NX], qd[R], gl[R], xo[R][C], jsum[C];
     load_rows<NX, R, C>(a, rg * R, d, qd, gl, xo);
     pdl_wait_primary();
     const uint32_t gen = a.gen ? *a.gen : 0u;
     fill_knots<false>(a, Us, xs, par, c0, ptile, gen, tid, blockDim.x);  // ends with a barrier
-    if (a.box_mode)
+    if (hooks)
         horizon_loop<NX, R, C, false, true>(a, d, X, NX, xs, BTs, NX, Us, ks, rg * R, cg * C, xo,
                                             qd, gl, jsum, Bx);
     else
@@ -207,7 +208,7 @@ size_t rollout_smem_bytes(const TileShape& s, int n, int m, int p, int T) {
         const int xsw = round_up(cpw, 4);
         const int per_warp = round_up(2 * xr * xsw + m * p * xsw + 2 * xsw, 4);
         const int head = round_up(m * xr, 4) + 4 * T + round_up(n * (s.nx + 2), 4) +
-                         round_up(3 * xr, 4);
+                         round_up(4 * xr, 4);
         return sizeof(float) * (size_t)(head + s.groups * per_warp);
     }
     const BlockLayout L(s.nx, s.groups * s.cands, m, p, T);

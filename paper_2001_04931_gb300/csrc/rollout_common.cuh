@@ -419,13 +419,25 @@ __device__ __forceinline__ float box_hook(const float* bx, int ld, int row, int 
     return (mode & 1) ? fminf(fmaxf(x, lo), hi) : x;
 }
 
-// Stage the box of rows 0 .. ld-1 into shared memory (padding rows never bind).
+// Whether a rollout runs the hooked copy of its horizon loop: a state box
+// or a constant disturbance.
+__device__ __forceinline__ bool has_hooks(const RolloutArgs& a) {
+    return a.box_mode != 0 || a.wd != nullptr;
+}
+
+// Stage the hooks of rows 0 .. ld-1 into shared memory as [4][ld]: lo, hi,
+// rho of the state box (a box that never binds without one, and on padding
+// rows) and the disturbance w_d (zero without one).
 __device__ __forceinline__ void stage_box(const RolloutArgs& a, float* bx, int ld, int t,
                                           int nt) {
-    for (int i = t; i < 3 * ld; i += nt) {
+    for (int i = t; i < 4 * ld; i += nt) {
         const int which = i / ld, row = i - which * ld;
-        const float pad = which == 0 ? -INFINITY : which == 1 ? INFINITY : 0.0f;
-        bx[i] = row < a.n ? a.box[which * a.n + row] : pad;
+        float v = which == 0 ? -INFINITY : which == 1 ? INFINITY : 0.0f;
+        if (row < a.n) {
+            if (which < 3 && a.box_mode) v = a.box[which * a.n + row];
+            if (which == 3 && a.wd) v = a.wd[row];
+        }
+        bx[i] = v;
     }
 }
 
@@ -442,7 +454,8 @@ namespace empc {
 // in registers; BU pairs are refreshed at knot-segment changes; the stage
 // cost is accumulated in 16-step blocks.  One barrier (warp or block) per
 // step separates the double-buffered state reads from the writes.  BOX
-// compiles in the state-box hook (bx).
+// compiles in the hooks staged at bx (stage_box): the disturbance w_d, then
+// the state box.
 template <int NX, int R, int C, bool WARP, bool BOX = false>
 __device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (&d)[R][NX],
                                              float* X, int xrows, int xs, const float* BTs,
@@ -490,7 +503,10 @@ __device__ __forceinline__ void horizon_loop(const RolloutArgs& a, const float (
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 xn[c] = xo[r][c] + acc[r][c];
-                if constexpr (BOX) xn[c] = box_hook(bx, xrows, row0 + r, a.box_mode, xn[c], jblk[c]);
+                if constexpr (BOX) {
+                    xn[c] = xn[c] + bx[3 * xrows + row0 + r];  // w_d
+                    xn[c] = box_hook(bx, xrows, row0 + r, a.box_mode, xn[c], jblk[c]);
+                }
                 xo[r][c] = xn[c];
                 const float e = xn[c] - gl[r];
                 jblk[c] = fmaf(qd[r] * e, e, jblk[c]);

@@ -38,7 +38,7 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
     KnotStep* ks = reinterpret_cast<KnotStep*>(smem + round_up(m * XR, 4));
     float* Ds = smem + round_up(m * XR, 4) + 4 * T;
     float* Bx = Ds + round_up(a.n * DS, 4);
-    float* W = Bx + round_up(3 * XR, 4) + warp * warp_slice_floats<NX, C>(m * a.p);
+    float* W = Bx + round_up(4 * XR, 4) + warp * warp_slice_floats<NX, C>(m * a.p);
     const int c0 = a.cand_begin + (blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
     pdl_launch_dependents();
     for (int i = threadIdx.x; i < m * XR; i += blockDim.x) {
@@ -50,10 +50,11 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
         const int r = i / DS, k = i % DS;
         Ds[i] = k < a.n ? a.D[r * a.n + k] : 0.0f;
     }
-    if (a.box_mode) stage_box(a, Bx, XR, threadIdx.x, blockDim.x);
+    const bool hooks = has_hooks(a);
+    if (hooks) stage_box(a, Bx, XR, threadIdx.x, blockDim.x);
     __syncthreads();
     if (c0 >= a.P) return;  // no block barrier follows
-    warp_tile<NX, C>(a, c0, W, BTs, ks, Ds, DS, a.box_mode ? Bx : nullptr);
+    warp_tile<NX, C>(a, c0, W, BTs, ks, Ds, DS, hooks ? Bx : nullptr);
 }
 
 template <int NX, int C>

@@ -23,7 +23,8 @@ __host__ __device__ constexpr int nrg_of(int nx) {
 
 // The horizon loop of rollout_common.cuh's horizon_loop on the
 // pair-interleaved state tile, with paired FMAs and two partial sums per
-// output (state_product_pairs).  BOX compiles in the state-box hook (bx).
+// output (state_product_pairs).  BOX compiles in the hooks staged at bx
+// (stage_box): the disturbance w_d, then the state box.
 template <int NX, int R, int C, bool BOX>
 __device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
                                                    const float2 (&d2)[R][NX / 2], float* X,
@@ -73,7 +74,10 @@ __device__ __forceinline__ void horizon_loop_pairs(const RolloutArgs& a,
             for (int c = 0; c < C; ++c) {
                 const float sum = acc[r][c].x + acc[r][c].y;
                 float xn = xo[r][c] + sum;
-                if constexpr (BOX) xn = box_hook(bx, xrows, row0 + r, a.box_mode, xn, jblk[c]);
+                if constexpr (BOX) {
+                    xn = xn + bx[3 * xrows + row0 + r];  // w_d
+                    xn = box_hook(bx, xrows, row0 + r, a.box_mode, xn, jblk[c]);
+                }
                 xo[r][c] = xn;
                 const float e = xn - gl[r];
                 jblk[c] = fmaf(qd[r] * e, e, jblk[c]);
@@ -107,8 +111,8 @@ __host__ __device__ constexpr int warp_slice_floats(int D) {
 // problem `a` and writes their costs.  W is the warp's shared-memory slice;
 // BTs ([m][XR], rows past n zero) and ks (knot table) are staged by the CTA,
 // and so is D when Ds is given ([n][ds] with ds >= NX, columns past n zero;
-// otherwise the rows are read from global memory).  bx, if given, is the
-// state box staged as [3][XR] (stage_box) and turns on the hook.
+// otherwise the rows are read from global memory).  bx, if given, holds the
+// hooks staged as [4][XR] (stage_box) and selects the hooked loop.
 // Reads the population, the elites and the generation counter only after
 // pdl_wait_primary(); COHERENT reads them through L2 (persistent kernels).
 template <int NX, int C, bool COHERENT = false>

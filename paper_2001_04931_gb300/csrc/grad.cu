@@ -29,7 +29,6 @@ struct GradGeom {
     static constexpr int R = (NX + NRG - 1) / NRG;
     static constexpr int XR = NRG * R;
     static constexpr int CGW = 32 / NRG;
-    static constexpr int LDD = NX + 1;  // padded row of D in shared memory
 };
 
 // Per-warp shared-memory slice (floats).

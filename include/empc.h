@@ -155,7 +155,8 @@ enum { EMPC_BOX_CLAMP = 1, EMPC_BOX_PENALTY = 2 };
  * simulated, hard stops and non-convex state costs can be written into the
  * simulation as if/else).  Per state i, host FP32 arrays of n entries:
  * lo [n] (NULL: -inf), hi [n] (NULL: +inf), rho [n] (NULL: 0).  After every
- * update x_{k+1} = A_d x_k + B_d u_k, for each state, in this order:
+ * update x_{k+1} = A_d x_k + B_d u_k (+ w_d, empc_set_disturbance), for each
+ * state, in this order:
  *   d_i = max(0, lo_i - x_i, x_i - hi_i)   (distance outside the box)
  *   EMPC_BOX_PENALTY:  J += rho_i d_i^2      (soft state limit)
  *   EMPC_BOX_CLAMP:    x_i = min(max(x_i, lo_i), hi_i)   (hard stop)
@@ -167,7 +168,8 @@ enum { EMPC_BOX_CLAMP = 1, EMPC_BOX_PENALTY = 2 };
  * EMPC_EINVAL unless lo_i <= hi_i, lo_i < +inf, hi_i > -inf and rho_i is
  * finite and >= 0 (NaN fails), or on unknown flag bits; EMPC_EUNSUPPORTED
  * with a non-zero flag for BF16 precision, the condensed evaluator or
- * refinement (none of them simulates the states one by one).
+ * refinement (none of them simulates the states one by one); while a box is
+ * set, empc_grad returns EMPC_EUNSUPPORTED too.
  */
 empc_status empc_set_state_box(empc_handle h, const float* lo, const float* hi,
                                const float* rho, int flags);

@@ -84,6 +84,25 @@ def test_costs_with_disturbance_match_oracle(kw):
         prob.close()
 
 
+def test_large_state_block_family_with_hooks():
+    """n = 80 runs only in the block family (state class 128, padded rows)."""
+    wl = W.small(dof=40, T=20, p=3, P=64, E=4)
+    w = _w(wl.n, 9)
+    M = _oracle(wl, w)
+    x0, g = wl.start_goal()
+    pop = np.random.default_rng(8).uniform(-1, 1, (wl.m * wl.p, wl.P)).astype(np.float32)
+    prob = gpu_problem(wl)
+    assert prob.info().tile_kind == 0
+    prob.set_disturbance(w)
+    lo, hi = np.full(wl.n, -0.25, np.float32), np.full(wl.n, 0.25, np.float32)
+    rho = np.full(wl.n, 8.0, np.float32)
+    prob.set_state_box(lo, hi, rho, clamp=True, penalty=True)
+    ref = M.cost_population(x0, g, pop, box=O.StateBox(lo, hi, rho, clamp=True, penalty=True))
+    got = _evaluate(prob, x0, g, pop)
+    assert rel_err(got, ref).max() <= COST_RTOL
+    prob.close()
+
+
 def test_zero_disturbance_is_none_bitwise():
     wl = W.small(dof=4, T=30, p=4, P=96, E=8)
     x0, g = wl.start_goal()

@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--evaluator", default="rollout", choices=["rollout", "condensed"],
                     help="population costs by rollout (default) or by the condensed quadratic "
                          "form of the linear-quadratic problem (c1, c2 only)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="c2 only: leave out the refined, batched and BF16 variant records "
+                         "(profiling runs)")
+    ap.add_argument("--compare-seeds", type=int, default=5,
+                    help="seeded instances for the variant-against-FP32 comparisons")
     ap.add_argument("--tile", type=int, default=0,
                     help="1-based rollout tile shape to force (0: autotune); profiling "
                          "runs use it so that the profiled launches match a plain run")
@@ -80,7 +85,8 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 10 ms (as fast as
+    nvidia-smi delivers them)."""
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -92,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", idx, f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "10"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
 
@@ -113,7 +119,7 @@ class ClockSampler:
             except ValueError:
                 continue
             rows.append((ts, sm, smax, f[5:9]))
-        inside = [r for r in rows if t0 - 0.25 <= r[0] <= t1 + 0.25] or rows
+        inside = [r for r in rows if t0 - 0.02 <= r[0] <= t1 + 0.02] or rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v == "Active"})
         sms = [r[1] for r in inside]
@@ -394,10 +400,49 @@ def run_gpu(args, wl, rank, world, local_rank):
         line = run_batched(args, rank, world, local_rank, dist, stream, flush)
     else:
         line = run_single(args, rank, world, local_rank, dist, stream, flush)
+    if args.workload == "c2" and world == 1 and not args.no_variants and args.evaluator == "rollout":
+        line["variants"] = run_variants(args, rank, world, local_rank, stream, flush)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def compact(line):
+    """The figures of a workload's bench line that its variant record keeps."""
+    roof = line["roofline"]
+    keep = ("bound", "kernel", "achieved", "peak", "unit", "frac", "peak_basis", "launch_us",
+            "flops_per_launch", "epilogue_fp32")
+    out = {"workload": line["config"]["workload"], "dtype": line["dtype"],
+           "metric": line["metric"], "value": line["value"], "unit": line["unit"],
+           "steps": line["steps"], "warmup": line["warmup"],
+           "ms_per_step": line["ms_per_step"], "ms_per_problem": line["ms_per_problem"],
+           "e2e": line["e2e"], "gpu_launches": line["gpu_launches"], "clocks": line["clocks"],
+           "roofline": {k: roof[k] for k in keep if k in roof}}
+    for k in ("compare", "bf16_cost_error"):
+        if k in line:
+            out[k] = line[k]
+    return out
+
+
+def run_variants(args, rank, world, local_rank, stream, flush):
+    """The other workloads beside the headline one, each timed like it (its
+    own warm-up, K timed solves, clock samples) and compared with plain FP32
+    EMPC on the same GPU: c3 (refined), c5 (BF16 tensor cores) and c4 (256
+    problems in one persistent launch)."""
+    import copy
+    out = {}
+    for name in ("c3", "c5", "c4"):
+        va = copy.copy(args)
+        va.workload, va.tile, va.no_cpu_baseline = name, 0, True
+        va.e2e_steps = min(args.e2e_steps, 10)
+        va.compare_seeds = min(args.compare_seeds, 1 if name == "c4" else 3)
+        if name == "c4":
+            line = run_batched(va, rank, world, local_rank, None, stream, flush)
+        else:
+            line = run_single(va, rank, world, local_rank, None, stream, flush)
+        out[name] = compact(line)
+    return out
 
 
 def run_single(args, rank, world, local_rank, dist, stream, flush):
@@ -485,7 +530,8 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
         loop = closed_loop_line(E, wl, A, B, 1 + rank, not args.no_cpu_baseline)
         box = state_box_line(E, wl, A, B, 1 + rank)
     if wl.name in ("c3", "c5") and rank == 0:
-        compare = compare_variant(E, wl.name)
+        compare = compare_variant(E, wl.name, tuple(range(args.compare_seeds)))
+    bf16_err = bf16_population_error(prob, wl, x0, g) if bf16 and rank == 0 else None
     # per generation: breed, rollout, select (+ the refinement kernel after the first;
     # + one adjoint launch per solve for the condensed terms)
     launches = wl.G * 3 + (wl.G - 1 if wl.name == "c3" else 0) + (1 if condensed else 0)
@@ -510,9 +556,28 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
         "clocks": clocks,
         "cpu_baseline": cpu,
         **({"compare": compare} if compare else {}),
+        **({"bf16_cost_error": bf16_err} if bf16_err else {}),
         **({"closed_loop": loop} if loop else {}),
         **({"state_box": box} if box else {}),
     }
+
+
+def bf16_population_error(prob, wl, x0, g, sample=256):
+    """Per-candidate BF16 cost error against the FP64 oracle on the
+    workload itself: `sample` candidates of the population the last timed
+    solve left (the search's own, evolved candidates), each costed by the
+    oracle; max and median relative error."""
+    import torch
+    pop = torch.empty((prob.D, prob.P), device="cuda")
+    cost = torch.empty(prob.P, device="cuda")
+    prob.get_state(pop, cost, None)
+    torch.cuda.synchronize()
+    pop, cost = pop.cpu().numpy(), cost.cpu().numpy()
+    cols = np.sort(np.random.default_rng(0).choice(prob.P, sample, replace=False))
+    oc = oracle_plan_costs(wl, x0, g, pop[:, cols])
+    err = np.abs(cost[cols] - oc) / np.abs(oc)
+    return {"sample": f"{sample} of the {prob.P} candidates of the last solve's population",
+            "max_rel": float(err.max()), "median_rel": float(np.median(err))}
 
 
 def closed_loop_line(E, wl, A, B, seed, with_oracle):
@@ -583,12 +648,23 @@ def _timed_solve(prob, x0, g, G):
     return 1e3 * (time.perf_counter() - t0), k, c
 
 
+def oracle_plan_costs(wl, x0, g, plans):
+    """FP64 costs of host plans [m*p, k] by the oracle's own discretization and
+    rollout (CPU leg of the bench)."""
+    import oracle as O
+    A, B = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+    b = wl.bounds()
+    M = O.Model(A, B, wl.Q(), wl.R(), b[:, 0], b[:, 1], wl.T, wl.p)
+    return M.cost_population(x0, g, np.ascontiguousarray(plans, np.float32))
+
+
 def compare_variant(E, name, seeds=(0, 1, 2, 3, 4)):
     """The workload's variant (c3: refined, c5: BF16) against plain FP32 EMPC
     on the same GPU, over seeded instances (plant, start and goal): solve time
-    (host-timed, graphs already captured) and the final plans' costs, both
-    re-evaluated by the FP32 rollout.  c3 also reports how many generations
-    (and how long) plain EMPC needs to come within 1% of the refined cost."""
+    (host-timed, graphs already captured) and the final plans' costs,
+    re-evaluated both by the FP32 rollout and by the FP64 oracle.  c3 also
+    reports how many generations (and how long) plain EMPC needs to come
+    within 1% of the refined cost."""
     import torch
     rows = []
     for s in seeds:
@@ -609,8 +685,11 @@ def compare_variant(E, name, seeds=(0, 1, 2, 3, 4)):
                       torch.tensor(g, dtype=torch.float32, device="cuda"), pop, cost)
         torch.cuda.synchronize()
         cv, cb = cost.cpu().numpy().tolist()
+        ov, ob = oracle_plan_costs(wl, x0, g, np.stack([k_v, k_b], 1)).tolist()
         row = {"seed": s, "variant_ms_per_solve": ms_v, "fp32_ms_per_solve": ms_b,
-               "variant_final_cost": cv, "fp32_final_cost": cb, "final_cost_ratio": cv / cb}
+               "variant_final_cost": cv, "fp32_final_cost": cb, "final_cost_ratio": cv / cb,
+               "variant_final_cost_fp64": ov, "fp32_final_cost_fp64": ob,
+               "final_cost_ratio_fp64": ov / ob}
         if name == "c3":
             base.reset()
             gens, best, t_ms = 0, float("inf"), 0.0
@@ -627,6 +706,9 @@ def compare_variant(E, name, seeds=(0, 1, 2, 3, 4)):
     med = lambda k: float(np.median([r[k] for r in rows]))
     return {"variant": "refined" if name == "c3" else "bf16", "seeds": rows,
             "median_final_cost_ratio": med("final_cost_ratio"),
+            "median_final_cost_ratio_fp64": med("final_cost_ratio_fp64"),
+            "max_final_cost_deviation_fp64": float(max(abs(r["final_cost_ratio_fp64"] - 1.0)
+                                                       for r in rows)),
             "median_variant_ms": med("variant_ms_per_solve"),
             "min_variant_ms": float(min(r["variant_ms_per_solve"] for r in rows)),
             "median_fp32_ms": med("fp32_ms_per_solve"),
@@ -713,7 +795,8 @@ def run_batched(args, rank, world, local_rank, dist, stream, flush):
     peak, basis, measured = fp32_peak(E, clocks, local_rank)
     flops = sum(alg_flops_per_candidate(wl) * wl.P for wl in wls) * G
     achieved = flops / (ms_step * 1e-3) / 1e12
-    compare = compare_batched(E, G, rank) if rank == 0 else None
+    compare = (compare_batched(E, G, rank, tuple(range(min(args.compare_seeds, 3))))
+               if rank == 0 else None)
     cpu = None if args.no_cpu_baseline else cpu_baseline_batch(wls, args.cpu_seconds)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -43,3 +43,15 @@ def check_elites(gpu_elite, orc_cost, E, rtol=2e-5):
     assert not (set(above.tolist()) & sel)
     c = key[gpu_elite]
     assert (c[1:] >= c[:-1] * (1 - rtol) - 1e-30).all()
+
+
+def report(name, **values):
+    """Append measured figures (errors, bounds) as one JSON line to the file
+    named by EMPC_TEST_REPORT, when set; tests still assert their bars."""
+    import json
+    import os
+    path = os.environ.get("EMPC_TEST_REPORT")
+    if not path:
+        return
+    with open(path, "a") as f:
+        f.write(json.dumps({"test": name, **{k: float(v) for k, v in values.items()}}) + "\n")

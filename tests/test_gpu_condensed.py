@@ -6,6 +6,9 @@ host's FP64 Hessian and g, c0 from one FP32 adjoint evaluation at U = 0.  Its
 rounding acts on the three terms, not on their (possibly much smaller) sum,
 so the bar is stated against their size: |J_gpu - J_fp64| <= 1e-5 (|U'HU| +
 |g'U| + |c0|), with g = 2f and H, f, c0 the oracle's FP64 condensed form.
+On these workloads the terms do not cancel much, and the error relative to
+J itself is held to the rollout's bar as well: |J_gpu - J_fp64| <= 1e-5 |J|
+(measured: at most about 5e-7).
 Breeding is the same kernel as with the rollout, so populations match the
 oracle bit for bit; the elite set must agree wherever the FP64 costs are
 separated by more than the evaluator's error bound."""
@@ -14,7 +17,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import check_elites, gpu_problem, oracle_model
+from helpers import check_elites, gpu_problem, oracle_model, report
 
 pytestmark = pytest.mark.gpu
 TERM_RTOL = 1e-5
@@ -53,7 +56,10 @@ def _lockstep(wl, generations, seed=5, sample=None):
         oc = M.cost_population(x0, g, pop[:, cols])
         scale = np.abs(np.einsum("ic,ij,jc->c", U, H, U)) + np.abs(2.0 * f @ U) + abs(c0)
         err = np.abs(cost[cols] - oc)
+        report(f"condensed_n{wl.n}_P{wl.P}_gen{gen}", max_rel_terms=np.max(err / scale),
+               max_rel_J=np.max(err / np.abs(oc)))
         assert (err <= TERM_RTOL * scale).all(), float(np.max(err / scale))
+        assert (err <= TERM_RTOL * np.abs(oc)).all(), float(np.max(err / np.abs(oc)))
         if sample is None:
             check_elites(el, oc, wl.E, rtol=2.0 * float(np.max(TERM_RTOL * scale / np.abs(oc))))
         assert best == cost[el[0]]

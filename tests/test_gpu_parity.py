@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from helpers import check_elites, gpu_problem, oracle_model, rel_err
+from helpers import check_elites, gpu_problem, oracle_model, rel_err, report
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,9 @@ def _lockstep(wl, generations, seed=3, sample=None, **cfg):
         cols = np.arange(wl.P) if sample is None else np.unique(
             np.r_[sample, elite, np.arange(min(wl.E, wl.P))])
         oc = M.cost_population(x0, g, pop[:, cols])
-        assert rel_err(cost[cols], oc).max() <= COST_RTOL
+        err = rel_err(cost[cols], oc)
+        report(f"lockstep_n{wl.n}_P{wl.P}_gen{gen}", max_rel=err.max())
+        assert err.max() <= COST_RTOL
         if sample is None:
             check_elites(elite, oc, wl.E)
         # the reported best is rank 0
@@ -91,9 +93,41 @@ def test_lockstep_gate_modes(gate):
     _lockstep(W.small(dof=2, T=17, p=3, P=96, E=8, sigma=0.3), 3, gate=gate)
 
 
-def test_lockstep_c2_full_size_sampled():
-    rng = np.random.default_rng(0)
-    _lockstep(W.config("c2"), 3, sample=rng.choice(4096, 96, replace=False))
+def test_lockstep_c2_full_size():
+    # every one of the 4096 candidates costed by the FP64 oracle, and the
+    # elite set checked, in each of three lockstep generations
+    _lockstep(W.config("c2"), 3)
+
+
+def _c5_fp32_workload(P=512, T=200):
+    """The 64-DoF chain of the large workload (n = 128, m = 64, 8 knots) at a
+    population the oracle costs in seconds: four tiles of 128 plus a ragged
+    tail when P is not a multiple of 128."""
+    return W.small(dof=64, radius=3, dt=0.005, T=T, p=8, P=P, E=16, q_pos=10.0, q_vel=1.0,
+                   r=1e-4)
+
+
+def test_fp32_block_family_n128_costs():
+    """n = 128 runs in the block family with one state row per thread (R = 1):
+    the plain-FP32 path the BF16 rollout of the 64-DoF chain is compared with.
+    Horizon 200 as in that workload; 4.5 tiles of candidates."""
+    wl = _c5_fp32_workload(P=577)
+    prob = gpu_problem(wl)
+    inf = prob.info()
+    assert inf.tile_kind == 0 and inf.tile_nx == 128 and inf.tile_rows == 1
+    M = oracle_model(wl)
+    x0, g = wl.start_goal()
+    pop = np.random.default_rng(3).uniform(-1, 1, (wl.m * wl.p, wl.P)).astype(np.float32)
+    err = rel_err(_evaluate(prob, x0, g, pop), M.cost_population(x0, g, pop))
+    report("fp32_block_n128_T200", max_rel=err.max(), median_rel=np.median(err))
+    assert err.max() <= COST_RTOL, (float(err.max()), float(np.median(err)))
+    prob.close()
+
+
+def test_lockstep_fp32_n128():
+    """Two lockstep generations of the 64-DoF chain in FP32 (block family):
+    bred populations bit-exact, every cost within 1e-5, elites checked."""
+    _lockstep(_c5_fp32_workload(P=384, T=120), 2)
 
 
 @pytest.mark.parametrize("kw", [

@@ -221,6 +221,36 @@ def test_refine_descends_and_stays_in_bounds():
         U, J = U2, J2
 
 
+@pytest.mark.parametrize("eta_scale,steps", [(1.0, 1), (1.0, 3), (40.0, 1), (40.0, 2)])
+def test_refine_is_the_projected_step_of_the_condensed_form(eta_scale, steps):
+    """orc_refine against projected gradient written out in numpy from the
+    condensed form J = U'HU + 2f'U + c0 (Sec. IV-E), whose S is pinned to the
+    printed example: each step is U <- clip(U - eta (2 H U + 2 f)) with each
+    knot clipped to its own input's bounds.  The large step makes clipping
+    bind on many knots, so a clip taken before the step, a missing factor 2,
+    a wrong step count or a wrong input index for the bounds all fail."""
+    wl = W.small(dof=3, T=30, p=4)
+    Ad, Bd = O.zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+    lo = np.array([-1.0, -0.3, -0.7])
+    hi = np.array([0.9, 0.4, 1.0])
+    M = O.Model(Ad, Bd, wl.Q(), wl.R(), lo, hi, wl.T, wl.p)
+    x0, g = wl.start_goal()
+    H, f, _ = M.condensed(x0, g)
+    eta = eta_scale * M.lipschitz_step()
+    lo_q, hi_q = np.repeat(lo, wl.p), np.repeat(hi, wl.p)
+    U0 = np.random.default_rng(5).uniform(lo_q, hi_q)
+    U = U0.copy()
+    clipped = 0
+    for _ in range(steps):
+        free = U - eta * (2.0 * H @ U + 2.0 * f)
+        U = np.minimum(np.maximum(free, lo_q), hi_q)
+        clipped += int(np.count_nonzero(U != free))
+    got = M.refine(x0, g, U0, steps, eta)
+    np.testing.assert_allclose(got, U, rtol=1e-10, atol=1e-12)
+    if eta_scale > 1.0:
+        assert clipped >= 3  # the bounds bind, so the clip's place in the step matters
+
+
 # ------------------------------------------------------------------ ZOH
 def test_zoh_matches_scipy_expm():
     plant = W.chain_plant(4, seed=3, radius=3)

@@ -100,9 +100,19 @@ void empc_config_default(empc_config* cfg);
  * empc_create - build a problem on the current CUDA device.
  *   A [n*n], B [n*m]  discrete model x_{k+1} = A x_k + B u_k (Eq.
  *                     first_order_integration, w_d = 0); host FP64.
- *   Q [n*n], R [m*m]  cost weights of Eq. mpc_problem (u_goal = 0); host FP64.
- *                     Must be diagonal with non-negative entries (else
- *                     EMPC_EUNSUPPORTED / EMPC_EINVAL).
+ *   Q [n*n], R [m*m]  cost weights of Eq. mpc_problem (u_goal = 0); host FP64,
+ *                     dense or diagonal.  Only their symmetric parts enter the
+ *                     cost; those must be positive semidefinite (else
+ *                     EMPC_EINVAL).  A diagonal Q is used as it is.  A
+ *                     non-diagonal Q is diagonalized on the host (Q_s = V
+ *                     diag(lambda) V', FP64 Jacobi) and every rollout runs in
+ *                     z = V'x, where the model is V'AV, V'B and the weight
+ *                     diag(lambda): the same J for every knot vector, with no
+ *                     per-step cost beyond the diagonal one.  Start states,
+ *                     goals and disturbances are rotated on the way in; the
+ *                     state box (empc_set_state_box), which acts on x, is then
+ *                     not available.  A non-diagonal R enters the input cost
+ *                     through the knot-weight Gram W: sum_ij R_ij U_i' W U_j.
  *   bounds [m*2]      (u_min, u_max) per input; knots are clipped to them.
  *   horizon T >= 1, knots p in [1, T] (Sec. IV-C), pop P >= 1, n <= 128.
  *   cfg               NULL for defaults.
@@ -219,24 +229,26 @@ empc_status empc_evaluate(empc_handle h, const float* dev_x0, const float* dev_g
                           const float* dev_pop, int count, float* dev_cost);
 
 /*
- * empc_evaluate_noalloc - empc_evaluate for callers that cannot allocate GPU
- * memory (a real-time control loop where cudaMalloc/cudaFree could stall
- * the device for an unbounded time, or a process whose GPU memory another
- * allocator reserved up front).  The paper has no counterpart; it is a
- * library addition.
- *   A [n*n], B [n*m], Q [n*n] (diagonal), R [m*m] (diagonal): host FP64,
- *     the same model as empc_create; horizon T and knots p as there.
+ * empc_evaluate_noalloc - empc_evaluate for callers that cannot allocate
+ * memory while they run (a real-time control loop where cudaMalloc/cudaFree
+ * could stall the device for an unbounded time, or a process whose GPU memory
+ * another allocator reserved up front).  The paper has no counterpart; it is
+ * a library addition.
+ *   A [n*n], B [n*m], Q [n*n], R [m*m]: host FP64, the same model and
+ *     weights as empc_create (dense or diagonal; symmetric parts positive
+ *     semidefinite, else EMPC_EINVAL); horizon T and knots p as there.
  *   dev_x0 [n], dev_goal [n], dev_pop [m*p][count] (SoA, stride count):
  *     device FP32 inputs; dev_cost [count]: device FP32 output.
  *   stream: a cudaStream_t (NULL = legacy default stream); asynchronous.
- * Allocates nothing: the per-problem tables live in one fixed device array
- * of 12,544 floats (49 KiB) that every device loading the library holds
- * until the process exits.  Limits: n <= 64, m <= 64, T <= 1024, p <= 64;
- * larger sizes return EMPC_EINVAL (use the handle API).  The first call on a
- * device looks up the array's device address; make that first call before
- * any stream capture.  Every call shares the array (each call rewrites what
- * it uses), so calls whose GPU work overlaps race and give wrong costs:
- * order them on one stream.  Non-diagonal Q or R: EMPC_EUNSUPPORTED.
+ * Allocates nothing, on the device or the host: the per-problem tables live
+ * in one fixed device array of 24,992 floats (about 98 KiB) that every
+ * device loading the library holds until the process exits; each call
+ * copies in only the floats its sizes need.  Limits: n <= 64, m <= 64,
+ * T <= 1024, p <= 64; larger sizes return EMPC_EINVAL (use the handle API).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture begins.  Every call shares the array,
+ * so calls whose GPU work overlaps race and give wrong costs: order them on
+ * one stream.  Failures leave a message for empc_last_error(NULL).
  */
 empc_status empc_evaluate_noalloc(const double* A, const double* B, const double* Q,
                                   const double* R, int n, int m, int horizon, int knots,
@@ -347,6 +359,9 @@ typedef struct {
  * (warps per CTA, candidates per lane) on a cold generation.  cfg supplies
  * the shared breeding parameters (p_cross_256, p_mutate_256, gate, sigma
  * default); cfg.tile > 0 forces launch shape tile-1.  FP32, no refinement.
+ * Q and R as in empc_create (dense or diagonal; a problem with a
+ * non-diagonal Q runs in Q's eigenbasis, its x0 and goal rotated on the
+ * host here and in empc_batch_set_targets).
  */
 empc_status empc_batch_create(const empc_problem_desc* probs, int count, const empc_config* cfg,
                               empc_batch* out);

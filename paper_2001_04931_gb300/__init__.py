@@ -180,15 +180,46 @@ def discretize_zoh(Ac, Bc, dt):
     return Ad, Bd
 
 
+def _noalloc_tensor(name, t, shape):
+    """A contiguous float32 CUDA tensor of `shape` on the current device, or
+    EmpcError(EMPC_EINVAL): the C side trusts these sizes."""
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and
+          t.is_contiguous() and tuple(t.shape) == tuple(shape) and
+          t.device.index == torch.cuda.current_device())
+    if not ok:
+        raise EmpcError(EMPC_EINVAL, f"{name} must be a contiguous float32 CUDA tensor of shape "
+                                     f"{tuple(shape)} on the current device")
+
+
 def evaluate_noalloc(A, B, Q, R, horizon, knots, x0, x_goal, pop, cost, stream=None):
-    """Population costs without device allocation (tables in a fixed device
-    array; see empc_evaluate_noalloc in include/empc.h).  x0, x_goal, pop
-    [m*p, count] and cost [count] are CUDA tensors; asynchronous on `stream`."""
+    """Population costs for callers that must not allocate memory while they
+    run (empc_evaluate_noalloc in include/empc.h: the tables live in a fixed
+    device array).  A [n, n], B [n, m], Q [n, n], R [m, m] are host arrays;
+    x0 and x_goal [n], pop [m*knots, count] and cost [count] are contiguous
+    float32 CUDA tensors on the current device; asynchronous on `stream` (a
+    cudaStream_t as an int, or None for the legacy default stream).  Every
+    shape is checked here (EmpcError EMPC_EINVAL) before the C call."""
     A, B, Q, R = _d(A), _d(B), _d(Q), _d(R)
+    if B.ndim != 2:
+        raise EmpcError(EMPC_EINVAL, "B must be [n, m]")
     n, m = B.shape
-    check(_lib.empc_evaluate_noalloc(_ptr(A), _ptr(B), _ptr(Q), _ptr(R), n, m, int(horizon),
-                                     int(knots), _dev(x0), _dev(x_goal), _dev(pop),
-                                     int(pop.shape[1]), _dev(cost), stream))
+    for name, M, k in (("A", A, n), ("Q", Q, n), ("R", R, m)):
+        if M.shape != (k, k):
+            raise EmpcError(EMPC_EINVAL, f"{name} must be [{k}, {k}]")
+    horizon, knots = int(horizon), int(knots)
+    if knots < 1:
+        raise EmpcError(EMPC_EINVAL, "knots must be >= 1")
+    _noalloc_tensor("x0", x0, (n,))
+    _noalloc_tensor("x_goal", x_goal, (n,))
+    if getattr(pop, "ndim", 0) != 2:
+        raise EmpcError(EMPC_EINVAL, "pop must be [m*knots, count]")
+    count = int(pop.shape[1])
+    _noalloc_tensor("pop", pop, (m * knots, count))
+    _noalloc_tensor("cost", cost, (count,))
+    check(_lib.empc_evaluate_noalloc(_ptr(A), _ptr(B), _ptr(Q), _ptr(R), n, m, horizon, knots,
+                                     _dev(x0), _dev(x_goal), _dev(pop), count, _dev(cost),
+                                     stream))
 
 
 def measure_fp32_peak():

@@ -47,6 +47,14 @@ struct empc_problem_s {
     // model, FP32 on device
     float *D_ = nullptr, *BT = nullptr, *qdiag = nullptr, *rdiag = nullptr, *gram = nullptr;
     float *umin = nullptr, *umax = nullptr, *x0 = nullptr, *goal = nullptr;
+    float* rmat = nullptr;     // dense symmetric R [m][m] (null when R is diagonal)
+    // non-diagonal Q: the rollouts run in z = Vt x (Q's eigenbasis); Vt in
+    // FP64 on the host and the device, and device scratch for rotated inputs
+    // of empc_evaluate / empc_grad
+    bool rotated = false;
+    std::vector<double> Vt_h;
+    double* Vt_dev = nullptr;
+    float *ev_x0 = nullptr, *ev_goal = nullptr;
     KnotStep* ktab = nullptr;
     // population state
     float* pop[2] = {nullptr, nullptr};
@@ -81,8 +89,8 @@ struct empc_problem_s {
     float* wd_dev = nullptr;
     std::vector<double> wd_h;
     bool has_wd = false;
-    // diag Q and diag R in FP64 (closed-loop actual cost)
-    std::vector<double> qd_h, rd_h;
+    // Q and R in FP64 (closed-loop actual cost)
+    std::vector<double> Q_h, R_h;
     // condensed evaluator: J(U) = U'HU + g'U + c0 (H padded to Dp x Dp)
     int Dp = 0;
     float *Hc = nullptr, *gvec = nullptr, *c0 = nullptr, *zero_knots = nullptr;
@@ -121,6 +129,7 @@ RolloutArgs base_args(empc_handle h) {
     a.BT = h->BT;
     a.qdiag = h->qdiag;
     a.rdiag = h->rdiag;
+    a.rmat = h->rmat;
     a.gram = h->gram;
     a.ktab = h->ktab;
     a.x0 = h->x0;
@@ -153,6 +162,7 @@ empc::GradArgs grad_args(empc_handle h) {
     g.BT = h->BT;
     g.qdiag = h->qdiag;
     g.rdiag = h->rdiag;
+    g.rmat = h->rmat;
     g.gram = h->gram;
     g.ktab = h->ktab;
     g.x0 = h->x0;
@@ -247,10 +257,10 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
 // The condensed Hessian H of J = U'HU + 2f'U + c in the knots (Sec. IV-E),
 // FP64, row-major D x D.  The columns of S (stacked states x_1..x_T per unit
 // knot, zero x0) come from rollouts of the parameterized dynamics;
-// H = S' Qbig S + sum_k Om_k' R Om_k with Q, R diagonal.
-std::vector<double> condensed_hessian(const double* A, const double* B,
-                                      const std::vector<double>& qd,
-                                      const std::vector<double>& rd, int n, int m, int T, int p,
+// H = S' Qbig S + sum_k Om_k' R Om_k, with the symmetric parts of Q and R
+// (dense or diagonal).
+std::vector<double> condensed_hessian(const double* A, const double* B, const double* Q,
+                                      const double* R, int n, int m, int T, int p,
                                       const std::vector<int>& idx, const std::vector<double>& w0,
                                       const std::vector<double>& w1) {
     const int D = m * p;
@@ -271,27 +281,41 @@ std::vector<double> condensed_hessian(const double* A, const double* B,
             for (int r = 0; r < n; ++r) S[((size_t)k * n + r) * D + q] = x[r];
         }
     }
-    std::vector<double> H((size_t)D * D, 0.0);
-    for (int k = 0; k < T; ++k)
-        for (int r = 0; r < n; ++r) {
-            const double* row = &S[((size_t)k * n + r) * D];
+    std::vector<double> H((size_t)D * D, 0.0), QS((size_t)n * D);
+    for (int k = 0; k < T; ++k) {
+        // QS = Q_s S_k, then H += S_k' QS
+        const double* Sk = &S[(size_t)k * n * D];
+        for (int r = 0; r < n; ++r)
             for (int a = 0; a < D; ++a) {
-                const double va = qd[r] * row[a];
-                if (va == 0.0) continue;
-                for (int b = 0; b < D; ++b) H[(size_t)a * D + b] += va * row[b];
+                double v = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    const double q = 0.5 * (Q[(size_t)r * n + j] + Q[(size_t)j * n + r]);
+                    if (q != 0.0) v += q * Sk[(size_t)j * D + a];
+                }
+                QS[(size_t)r * D + a] = v;
+            }
+        for (int r = 0; r < n; ++r) {
+            const double* row = &Sk[(size_t)r * D];
+            for (int a = 0; a < D; ++a) {
+                if (row[a] == 0.0) continue;
+                for (int b = 0; b < D; ++b) H[(size_t)a * D + b] += row[a] * QS[(size_t)r * D + b];
             }
         }
+    }
+    // input cost: u_k = sum_a w_ka U_a, so H[(i,a),(j,b)] += R_s,ij w_ka w_kb
     for (int k = 0; k < T; ++k)
-        for (int i = 0; i < m; ++i) {
-            const int a = i * p + idx[k];
-            H[(size_t)a * D + a] += rd[i] * w0[k] * w0[k];
-            if (p > 1) {
-                const int b = a + 1;
-                H[(size_t)b * D + b] += rd[i] * w1[k] * w1[k];
-                H[(size_t)a * D + b] += rd[i] * w0[k] * w1[k];
-                H[(size_t)b * D + a] += rd[i] * w0[k] * w1[k];
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                const double rij = 0.5 * (R[(size_t)i * m + j] + R[(size_t)j * m + i]);
+                if (rij == 0.0) continue;
+                const int a = i * p + idx[k], b = j * p + idx[k];
+                H[(size_t)a * D + b] += rij * w0[k] * w0[k];
+                if (p > 1) {
+                    H[(size_t)(a + 1) * D + (b + 1)] += rij * w1[k] * w1[k];
+                    H[(size_t)a * D + (b + 1)] += rij * w0[k] * w1[k];
+                    H[(size_t)(a + 1) * D + b] += rij * w1[k] * w0[k];
+                }
             }
-        }
     return H;
 }
 
@@ -321,6 +345,26 @@ double hessian_lambda_max(const std::vector<double>& H, int D) {
         lam = next;
     }
     return lam;
+}
+
+// Row i of the rollout coordinates of a host FP64 vector: (Vt v)_i in FP64
+// when the rollouts run in Q's eigenbasis, else v_i.
+double rotate_row(empc_handle h, const double* v, int i) {
+    if (!h->rotated) return v[i];
+    double s = 0.0;
+    for (int j = 0; j < h->n; ++j) s += h->Vt_h[(size_t)i * h->n + j] * v[j];
+    return s;
+}
+
+// Device start and goal in the rollout coordinates: rotated into (zx, zg)
+// when Q is not diagonal, else copied (or, with zx == x, used in place).
+cudaError_t stage_targets(empc_handle h, const float* x, const float* g, float* zx, float* zg) {
+    if (h->rotated) return empc::launch_rotate(h->Vt_dev, x, g, zx, zg, h->n, h->stream);
+    cudaError_t e = cudaSuccess;
+    if (zx != x) e = cudaMemcpyAsync(zx, x, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && zg != g)
+        e = cudaMemcpyAsync(zg, g, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+    return e;
 }
 
 empc_status run_generations(empc_handle h, int G) {
@@ -443,7 +487,7 @@ void free_handle(empc_handle h) {
                     h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
                     h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
                     h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev, h->box,
-                    h->wd_dev};
+                    h->wd_dev, h->rmat, h->Vt_dev, h->ev_x0, h->ev_goal};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->stage) cudaFreeHost(h->stage);
@@ -600,6 +644,12 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
          !empc::condensed_supported(m * knots)))
         return fail(nullptr, EMPC_EUNSUPPORTED,
                     "the condensed evaluator needs FP32, n <= 64, m*p <= 832 and no refinement");
+    empc::HostTables tb;
+    {
+        std::string msg;
+        const empc_status ts = empc::build_tables(A, B, Q, R, bounds, n, m, horizon, knots, tb, msg);
+        if (ts != EMPC_OK) return fail(nullptr, ts, msg);
+    }
     empc_handle h = new empc_problem_s();
     h->n = n;
     h->m = m;
@@ -631,9 +681,8 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     h->ce = cfg.ckpt_every > 0 ? std::min(cfg.ckpt_every, horizon)
                                : std::max(1, (int)std::ceil(std::sqrt((double)horizon)));
 
-    // host-side staging of the model in FP32
-    empc::HostTables tb;
-    empc::build_tables(A, B, Q, R, bounds, n, m, horizon, knots, tb);
+    // host-side staging of the model in FP32 (built before the device is touched)
+
     const std::vector<float>& Dm = tb.D;
     const std::vector<float>& BT = tb.BT;
     const std::vector<float>& qd = tb.qd;
@@ -649,11 +698,8 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
         if (cfg.refine_lr > 0.0f) {
             h->eta = cfg.refine_lr;
         } else {
-            std::vector<double> qdd(n), rdd(m);
-            for (int i = 0; i < n; ++i) qdd[i] = Q[(size_t)i * n + i];
-            for (int i = 0; i < m; ++i) rdd[i] = R[(size_t)i * m + i];
             const double lmax = hessian_lambda_max(
-                condensed_hessian(A, B, qdd, rdd, n, m, horizon, knots, idx, w0, w1), m * knots);
+                condensed_hessian(A, B, Q, R, n, m, horizon, knots, idx, w0, w1), m * knots);
             h->eta = lmax > 0.0 ? (float)(1.0 / (2.0 * lmax)) : 0.0f;
         }
     }
@@ -679,6 +725,14 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(dev_alloc(&h->gen, 1));
     EMPC_TRY(dev_alloc(&h->status, 1));
     EMPC_TRY(dev_alloc(&h->sigma_dev, 1));
+    if (tb.dense_r) EMPC_TRY(dev_alloc(&h->rmat, tb.rmat.size()));
+    h->rotated = tb.rotated;
+    if (tb.rotated) {
+        h->Vt_h = tb.Vt;
+        EMPC_TRY(dev_alloc(&h->Vt_dev, tb.Vt.size()));
+        EMPC_TRY(dev_alloc(&h->ev_x0, n));
+        EMPC_TRY(dev_alloc(&h->ev_goal, n));
+    }
     EMPC_TRY(cudaMallocHost(reinterpret_cast<void**>(&h->stage),
                             sizeof(float) * (2 * (size_t)n + D + 2)));
     cudaStream_t st = h->stream;
@@ -695,16 +749,17 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(cudaMemsetAsync(h->gen, 0, sizeof(uint32_t), st));
     EMPC_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
     EMPC_TRY(cudaMemcpyAsync(h->sigma_dev, &h->cfg.sigma, sizeof(float), cudaMemcpyHostToDevice, st));
-    h->qd_h.resize(n);
-    h->rd_h.resize(m);
-    for (int i = 0; i < n; ++i) h->qd_h[i] = Q[(size_t)i * n + i];
-    for (int i = 0; i < m; ++i) h->rd_h[i] = R[(size_t)i * m + i];
+    if (tb.dense_r)
+        EMPC_TRY(cudaMemcpyAsync(h->rmat, tb.rmat.data(), sizeof(float) * tb.rmat.size(),
+                                 cudaMemcpyHostToDevice, st));
+    if (tb.rotated)
+        EMPC_TRY(cudaMemcpyAsync(h->Vt_dev, tb.Vt.data(), sizeof(double) * tb.Vt.size(),
+                                 cudaMemcpyHostToDevice, st));
+    h->Q_h.assign(Q, Q + (size_t)n * n);
+    h->R_h.assign(R, R + (size_t)m * m);
     if (cfg.evaluator == EMPC_EVAL_CONDENSED) {
-        std::vector<double> qdd(n), rdd(m);
-        for (int i = 0; i < n; ++i) qdd[i] = Q[(size_t)i * n + i];
-        for (int i = 0; i < m; ++i) rdd[i] = R[(size_t)i * m + i];
         const std::vector<double> H =
-            condensed_hessian(A, B, qdd, rdd, n, m, horizon, knots, idx, w0, w1);
+            condensed_hessian(A, B, Q, R, n, m, horizon, knots, idx, w0, w1);
         h->Dp = empc::condensed_pad(h->D);
         std::vector<float> Hf((size_t)h->Dp * h->Dp, 0.0f);
         for (int a = 0; a < h->D; ++a)
@@ -759,8 +814,8 @@ empc_status empc_solve(empc_handle h, const double* x0, const double* x_goal, in
         return fail(h, EMPC_EINVAL, "non-finite x0 or x_goal");
     float* st_in = h->stage;
     for (int i = 0; i < h->n; ++i) {
-        st_in[i] = (float)x0[i];
-        st_in[h->n + i] = (float)x_goal[i];
+        st_in[i] = (float)rotate_row(h, x0, i);
+        st_in[h->n + i] = (float)rotate_row(h, x_goal, i);
     }
     EMPC_CUDA(h, cudaMemcpyAsync(h->x0, st_in, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
     EMPC_CUDA(h, cudaMemcpyAsync(h->goal, st_in + h->n, sizeof(float) * h->n, cudaMemcpyHostToDevice, h->stream));
@@ -799,6 +854,10 @@ empc_status empc_set_state_box(empc_handle h, const float* lo, const float* hi,
                   h->cfg.refine_steps > 0))
         return fail(h, EMPC_EUNSUPPORTED,
                     "the state-box hook needs the FP32 rollout evaluator without refinement");
+    if (flags && h->rotated)
+        return fail(h, EMPC_EUNSUPPORTED,
+                    "the state-box hook acts on the model's states; with a non-diagonal Q the "
+                    "rollouts run in Q's eigenbasis");
     const int n = h->n;
     std::vector<float> t(3 * (size_t)n);
     if (flags) {
@@ -840,7 +899,7 @@ empc_status empc_set_disturbance(empc_handle h, const double* w_d) {
         return fail(h, EMPC_EUNSUPPORTED, "the disturbance needs the FP32 rollout");
     if (nonzero) {
         std::vector<float> t(n);
-        for (int i = 0; i < n; ++i) t[i] = (float)w_d[i];
+        for (int i = 0; i < n; ++i) t[i] = (float)rotate_row(h, w_d, i);
         if (!h->wd_dev) EMPC_CUDA(h, dev_alloc(&h->wd_dev, (size_t)n));
         EMPC_CUDA(h, cudaMemcpyAsync(h->wd_dev, t.data(), sizeof(float) * n,
                                      cudaMemcpyHostToDevice, h->stream));
@@ -876,12 +935,12 @@ empc_status empc_closed_loop(empc_handle h, const double* Ad, const double* Bd, 
     std::vector<float> knots(h->D);
     auto stage = [&](const double* xs, const double* us) {
         double J = 0.0;
-        for (int i = 0; i < n; ++i) {
-            const double e = x_goal[i] - xs[i];
-            J += h->qd_h[i] * e * e;
-        }
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                J += (x_goal[i] - xs[i]) * h->Q_h[(size_t)i * n + j] * (x_goal[j] - xs[j]);
         if (us)
-            for (int i = 0; i < m; ++i) J += h->rd_h[i] * us[i] * us[i];
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) J += us[i] * h->R_h[(size_t)i * m + j] * us[j];
         return J;
     };
     double total = 0.0;
@@ -934,8 +993,7 @@ empc_status empc_solve_device(empc_handle h, const float* dev_x0, const float* d
     if (!dev_x0 || !dev_goal || !dev_best_knots || !dev_best_cost)
         return fail(h, EMPC_EINVAL, "NULL device pointer");
     if (generations < 1) return fail(h, EMPC_EINVAL, "generations must be >= 1");
-    EMPC_CUDA(h, cudaMemcpyAsync(h->x0, dev_x0, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, h->stream));
-    EMPC_CUDA(h, cudaMemcpyAsync(h->goal, dev_goal, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+    EMPC_CUDA(h, stage_targets(h, dev_x0, dev_goal, h->x0, h->goal));
     empc_status s = run_generations(h, generations);
     if (s != EMPC_OK) return s;
     EMPC_CUDA(h, cudaMemcpyAsync(dev_best_knots, h->best_knots, sizeof(float) * h->D, cudaMemcpyDeviceToDevice, h->stream));
@@ -953,6 +1011,11 @@ empc_status empc_evaluate(empc_handle h, const float* dev_x0, const float* dev_g
     RolloutArgs a = base_args(h);
     a.x0 = dev_x0;
     a.goal = dev_goal;
+    if (h->rotated) {
+        EMPC_CUDA(h, stage_targets(h, dev_x0, dev_goal, h->ev_x0, h->ev_goal));
+        a.x0 = h->ev_x0;
+        a.goal = h->ev_goal;
+    }
     a.mode = empc::kEval;
     a.P = count;
     a.pop_in = dev_pop;
@@ -977,6 +1040,11 @@ empc_status empc_grad(empc_handle h, const float* dev_x0, const float* dev_goal,
     empc::GradArgs g = grad_args(h);
     g.x0 = dev_x0;
     g.goal = dev_goal;
+    if (h->rotated) {
+        EMPC_CUDA(h, stage_targets(h, dev_x0, dev_goal, h->ev_x0, h->ev_goal));
+        g.x0 = h->ev_x0;
+        g.goal = h->ev_goal;
+    }
     g.pop_in = dev_pop;
     g.ld_in = count;
     g.count = count;

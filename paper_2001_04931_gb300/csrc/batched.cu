@@ -416,6 +416,7 @@ struct empc_batch_s {
     size_t result_floats = 0;        // floats from the best knots to the error word
     size_t off_costs_rel = 0, off_status_rel = 0, off_error_rel = 0;  // within that span
     std::vector<int> tgt_off;        // problem's offset in the x0 / goal blocks
+    std::vector<empc::HostTables> rot;  // per problem: its x -> z rotation (Vt) if Q is dense
     size_t tgt_floats = 0;           // floats of one block (x0 block, then goal block)
     float* d_targets = nullptr;      // device: x0 block | goal block
     float* h_targets = nullptr;      // pinned staging of the same
@@ -543,7 +544,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         return at;
     };
     struct Off {
-        size_t D, BT, qd, rd, gram, ks, lo, hi, pop0, pop1, cost, elite, ecost, gen, status;
+        size_t D, BT, qd, rd, rmat, gram, ks, lo, hi, pop0, pop1, cost, elite, ecost, gen, status;
     };
     std::vector<Off> off(count);
     for (int i = 0; i < count; ++i) {
@@ -568,7 +569,12 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
             free_batch(b);
             return bfail(nullptr, EMPC_EINVAL, "problem " + std::to_string(i) + ": bad elite count");
         }
-        empc::build_tables(d.A, d.B, d.Q, d.R, d.bounds, d.n, d.m, d.horizon, d.knots, tabs[i]);
+        vs = empc::build_tables(d.A, d.B, d.Q, d.R, d.bounds, d.n, d.m, d.horizon, d.knots,
+                                tabs[i], msg);
+        if (vs != EMPC_OK) {
+            free_batch(b);
+            return bfail(nullptr, vs, "problem " + std::to_string(i) + ": " + msg);
+        }
         b->n.push_back(d.n);
         b->m.push_back(d.m);
         b->T.push_back(d.horizon);
@@ -586,6 +592,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         o.BT = reserve((size_t)d.m * d.n);
         o.qd = reserve(d.n);
         o.rd = reserve(d.m);
+        o.rmat = tabs[i].dense_r ? reserve((size_t)d.m * d.m) : 0;
         o.gram = reserve(2 * (size_t)d.knots);
         o.ks = reserve(4 * (size_t)d.horizon);
         o.lo = reserve(d.m);
@@ -672,6 +679,11 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
     }
     float* base = reinterpret_cast<float*>(b->arena);
     b->h_probs.resize(count);
+    b->rot.resize(count);
+    for (int i = 0; i < count; ++i) {  // keep only what empc_batch_set_targets needs
+        b->rot[i].rotated = tabs[i].rotated;
+        b->rot[i].Vt = tabs[i].Vt;
+    }
     for (int i = 0; i < count; ++i) {
         const empc_problem_desc& d = probs[i];
         const empc::HostTables& t = tabs[i];
@@ -680,13 +692,19 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         put(o.BT, t.BT.data(), sizeof(float) * t.BT.size());
         put(o.qd, t.qd.data(), sizeof(float) * t.qd.size());
         put(o.rd, t.rd.data(), sizeof(float) * t.rd.size());
+        if (t.dense_r) put(o.rmat, t.rmat.data(), sizeof(float) * t.rmat.size());
         put(o.gram, t.gram.data(), sizeof(float) * t.gram.size());
         put(o.ks, t.ks.data(), sizeof(empc::KnotStep) * t.ks.size());
         put(o.lo, t.lo.data(), sizeof(float) * t.lo.size());
         put(o.hi, t.hi.data(), sizeof(float) * t.hi.size());
-        for (int k = 0; k < d.n; ++k) {
-            img[off_tgt + b->tgt_off[i] + k] = (float)d.x0[k];
-            img[off_tgt + b->tgt_floats + b->tgt_off[i] + k] = (float)d.x_goal[k];
+        {
+            std::vector<double> zx(d.n), zg(d.n);  // rollout coordinates (Q's eigenbasis)
+            t.rotate(d.x0, zx.data(), d.n);
+            t.rotate(d.x_goal, zg.data(), d.n);
+            for (int k = 0; k < d.n; ++k) {
+                img[off_tgt + b->tgt_off[i] + k] = (float)zx[k];
+                img[off_tgt + b->tgt_floats + b->tgt_off[i] + k] = (float)zg[k];
+            }
         }
         BatchProblem& bp = b->h_probs[i];
         std::memset(&bp, 0, sizeof(bp));
@@ -695,6 +713,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         a.BT = base + o.BT;
         a.qdiag = base + o.qd;
         a.rdiag = base + o.rd;
+        a.rmat = t.dense_r ? base + o.rmat : nullptr;
         a.gram = base + o.gram;
         a.ktab = reinterpret_cast<const empc::KnotStep*>(base + o.ks);
         a.x0 = base + off_tgt + b->tgt_off[i];
@@ -884,12 +903,17 @@ empc_status empc_batch_set_targets(empc_batch b, const double* x0, const double*
     EMPC_BCUDA(b, cudaEventSynchronize(b->tgt_done));
     float* h = b->h_targets;
     size_t at = 0;
+    std::vector<double> zx, zg;
     for (int i = 0; i < b->count; ++i) {
         float* hx = h + b->tgt_off[i];
         float* hg = h + b->tgt_floats + b->tgt_off[i];
+        zx.resize(b->n[i]);
+        zg.resize(b->n[i]);
+        b->rot[i].rotate(x0 + at, zx.data(), b->n[i]);
+        b->rot[i].rotate(x_goal + at, zg.data(), b->n[i]);
         for (int k = 0; k < b->n[i]; ++k) {
-            hx[k] = (float)x0[at + k];
-            hg[k] = (float)x_goal[at + k];
+            hx[k] = (float)zx[k];
+            hg[k] = (float)zg[k];
         }
         at += (size_t)b->n[i];
     }

@@ -22,8 +22,10 @@ struct RolloutArgs {
     // model
     const float* D;      // [n][n] row-major, D = A_d - I (delta form)
     const float* BT;     // [m][n] = B_d transposed
-    const float* qdiag;  // [n]   diagonal of Q
-    const float* rdiag;  // [m]   diagonal of R
+    const float* qdiag;  // [n]   state weights: diag(Q), or Q's eigenvalues when the
+                         //       rollouts run in Q's eigenbasis (non-diagonal Q)
+    const float* rdiag;  // [m]   diagonal of R (read when rmat is null)
+    const float* rmat;   // [m][m] symmetric R when it is not diagonal, else null
     const float* gram;   // [2p]  input-cost Gram: diag W_aa (p), off-diag W_a,a+1 (p)
     const KnotStep* ktab;  // [T]
     const float* x0;     // [n]
@@ -81,6 +83,7 @@ struct GradArgs {
     const float* BT;
     const float* qdiag;
     const float* rdiag;
+    const float* rmat;    // dense symmetric R [m][m], or null (diagonal, rdiag)
     const float* gram;
     const KnotStep* ktab;
     const float* x0;
@@ -169,6 +172,12 @@ cudaError_t launch_select(const float* cost, int P, int E, const float* pop, int
                           int* elite_idx, float* elite_cost, float* best_knots,
                           float* best_cost, uint32_t* gen, int* status, cudaStream_t st,
                           bool pdl = false);
+
+// z = Vt x and zg = Vt g for device vectors of n <= 128 entries: FP64 sums
+// of the FP64 rotation Vt [n][n] (row i = eigenvector i of Q), rounded once
+// to FP32 (rotate.cu).
+cudaError_t launch_rotate(const double* Vt, const float* x, const float* g, float* zx, float* zg,
+                          int n, cudaStream_t st);
 
 // Record a failure message for empc_last_error(NULL) on this thread; returns s.
 int set_thread_error(int s, const char* msg);

@@ -345,16 +345,28 @@ __global__ void grad_warp_kernel(const GradArgs a) {
                 }
         }
         __syncwarp();
-        // dJ/dU(i, a) = sum_r B(r, i) Lambda_a(r) + 2 r_i sum_b W_ab U(i, b)
+        // dJ/dU(i, a) = sum_r B(r, i) Lambda_a(r) + 2 sum_j R_ij sum_b W_ab U(j, b)
+        // (diagonal R: 2 r_i sum_b W_ab U(i, b))
+        auto wu_of = [&](int j, int aa, int t) {
+            const int q = j * p + aa;
+            float wu = a.gram[aa] * Us[q * XS + t];
+            if (aa > 0) wu = fmaf(a.gram[p + aa - 1], Us[(q - 1) * XS + t], wu);
+            if (aa + 1 < p) wu = fmaf(a.gram[p + aa], Us[(q + 1) * XS + t], wu);
+            return wu;
+        };
         for (int it = lane; it < D * CPW; it += 32) {
             const int q = it / CPW, t = it % CPW;
             const int i = q / p, aa = q % p;
             float gsum = 0.0f;
             for (int r = 0; r < n; ++r) gsum = fmaf(BTs[i * XR + r], LA[(aa * XR + r) * XS + t], gsum);
-            float wu = a.gram[aa] * Us[q * XS + t];
-            if (aa > 0) wu = fmaf(a.gram[p + aa - 1], Us[(q - 1) * XS + t], wu);
-            if (aa + 1 < p) wu = fmaf(a.gram[p + aa], Us[(q + 1) * XS + t], wu);
-            G[q * XS + t] = fmaf(2.0f * a.rdiag[i], wu, gsum);
+            float ru;
+            if (a.rmat) {
+                ru = 0.0f;
+                for (int j = 0; j < m; ++j) ru = fmaf(a.rmat[i * m + j], wu_of(j, aa, t), ru);
+            } else {
+                ru = a.rdiag[i] * wu_of(i, aa, t);
+            }
+            G[q * XS + t] = fmaf(2.0f, ru, gsum);
         }
         __syncwarp();
         if (a.steps == 0) {

@@ -7,13 +7,16 @@
 // by another framework's caching allocator.  The handle API (empc_create)
 // allocates its tables once per problem; this entry point instead keeps the
 // per-problem tables the cost kernel reads (D = A - I, B transposed, the Q
-// and R diagonals, the knot table and the input-cost Gram weights) in one
-// file-scope device array of fixed size, and allocates nothing.
+// and R weights, the knot table and the input-cost Gram weights, and for a
+// non-diagonal Q the rotation into its eigenbasis with the rotated start and
+// goal) in one file-scope device array of fixed size, and allocates nothing,
+// neither on the device nor on the host.
 //
-// Every call rewrites the part of the array it uses before its kernel reads
-// it, so nothing carries over between calls.  All calls in the process share
-// the array: two calls whose work overlaps on the GPU (different streams, or
-// different host threads without ordering) race on it and give wrong costs.
+// Every call writes the part of the array it uses before its kernels read
+// it (one copy of exactly the floats the call's sizes need), so nothing
+// carries over between calls.  All calls in the process share the array: two
+// calls whose work overlaps on the GPU (different streams, or different host
+// threads without ordering) race on it and give wrong costs.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,33 +25,63 @@
 
 #include "../../include/empc.h"
 #include "empc_internal.h"
+#include "host_tables.h"
 
 namespace {
 
-// Size limits of the shared table array (see include/empc.h).
+// Size limits of the shared table array (include/empc.h).  The rollout's
+// shared memory grows with n, m, p and T, and its largest case, n = m = p =
+// 64 and T = 1024, fits the one-warp tile of the warp-synchronous family
+// (about 117 KB), so every size within the limits has a tile.
 constexpr int kMaxN = 64;
 constexpr int kMaxM = 64;
 constexpr int kMaxT = 1024;
 constexpr int kMaxKnots = 64;
 
-// Float offsets of each table inside the array.
-constexpr int kOffD = 0;                             // [n][n]
-constexpr int kOffBT = kOffD + kMaxN * kMaxN;        // [m][n]
-constexpr int kOffQ = kOffBT + kMaxM * kMaxN;        // [n]
-constexpr int kOffR = kOffQ + kMaxN;                 // [m]
-constexpr int kOffGram = kOffR + kMaxM;              // [2 p]
-constexpr int kOffKnots = kOffGram + 2 * kMaxKnots;  // KnotStep[T] (4 floats each)
-constexpr int kScratchFloats = kOffKnots + 4 * kMaxT;
+// Floats of the array: D, BT, the Q and R weights, the Gram, the knot table
+// (4 floats a step), a dense R, the FP64 rotation (2 floats per entry), the
+// rotated start and goal, and alignment padding.
+constexpr int kScratchFloats = kMaxN * kMaxN + kMaxM * kMaxN + kMaxN + kMaxM + 2 * kMaxKnots +
+                               4 * kMaxT + kMaxM * kMaxM + 2 * kMaxN * kMaxN + 2 * kMaxN + 32;
 
-// The fixed scratch: 12,544 floats (49 KiB) on every device that loads the
-// library, held until the process exits.
+// The fixed scratch: 24,992 floats (about 98 KiB) on every device that loads
+// the library, held until the process exits.
 static __device__ __align__(256) float g_eval_tables[kScratchFloats];
 
-// Host staging for one call, and the per-device address of g_eval_tables.
+// Host staging of one call (guarded by g_mutex): the packed tables, then
+// FP64 knot weights, knot indices and the table builder's scratch.
 std::mutex g_mutex;
-float g_host_tables[kScratchFloats];
+alignas(16) float g_host_tables[kScratchFloats];
+double g_w0[kMaxT], g_w1[kMaxT];
+int g_idx[kMaxT];
+double g_work[3 * kMaxN * kMaxN + kMaxM * kMaxM + 2 * kMaxKnots];
 constexpr int kMaxDevices = 64;
 float* g_dev_tables[kMaxDevices] = {nullptr};
+
+empc_status reject(empc_status s, const char* msg) {
+    return (empc_status)empc::set_thread_error(s, msg);
+}
+
+// Float offsets of one call's tables inside the array (16-byte aligned
+// where a vector type or a double is read).
+struct Layout {
+    int D, BT, qd, rd, gram, ks, rmat, Vt, zx, zg, used;
+    Layout(int n, int m, int T, int p, bool dense_r, bool rotated) {
+        auto up4 = [](int v) { return (v + 3) / 4 * 4; };
+        D = 0;
+        BT = up4(D + n * n);
+        qd = up4(BT + m * n);
+        rd = up4(qd + n);
+        gram = up4(rd + m);
+        ks = up4(gram + 2 * p);
+        rmat = up4(ks + 4 * T);
+        Vt = up4(rmat + (dense_r ? m * m : 0));
+        zx = up4(Vt + (rotated ? 2 * n * n : 0));
+        zg = up4(zx + (rotated ? n : 0));
+        used = zg + (rotated ? n : 0);
+    }
+};
+static_assert(kScratchFloats == 24992, "the size stated in include/empc.h");
 
 }  // namespace
 
@@ -57,97 +90,86 @@ extern "C" empc_status empc_evaluate_noalloc(const double* A, const double* B, c
                                              int knots, const float* dev_x0,
                                              const float* dev_goal, const float* dev_pop,
                                              int count, float* dev_cost, void* stream) {
-    using empc::set_thread_error;
     if (!A || !B || !Q || !R || !dev_x0 || !dev_goal || !dev_pop || !dev_cost)
-        return (empc_status)set_thread_error(EMPC_EINVAL, "empc_evaluate_noalloc: NULL pointer");
+        return reject(EMPC_EINVAL, "empc_evaluate_noalloc: NULL pointer");
     if (n < 1 || n > kMaxN || m < 1 || m > kMaxM || horizon < 1 || horizon > kMaxT ||
         knots < 1 || knots > horizon || knots > kMaxKnots || count < 0)
-        return (empc_status)set_thread_error(
-            EMPC_EINVAL,
-            "empc_evaluate_noalloc: sizes beyond its fixed tables (n <= 64, m <= 64, "
-            "horizon <= 1024, knots <= 64, 1 <= knots <= horizon); use empc_create");
-    for (size_t i = 0; i < (size_t)n * n; ++i)
-        if (!std::isfinite(A[i]) || !std::isfinite(Q[i]))
-            return (empc_status)set_thread_error(EMPC_EINVAL, "non-finite A or Q");
-    for (size_t i = 0; i < (size_t)n * m; ++i)
-        if (!std::isfinite(B[i])) return (empc_status)set_thread_error(EMPC_EINVAL, "non-finite B");
-    for (size_t i = 0; i < (size_t)m * m; ++i)
-        if (!std::isfinite(R[i])) return (empc_status)set_thread_error(EMPC_EINVAL, "non-finite R");
+        return reject(EMPC_EINVAL,
+                      "empc_evaluate_noalloc: sizes beyond its fixed tables (n <= 64, m <= 64, "
+                      "horizon <= 1024, knots <= 64, 1 <= knots <= horizon, count >= 0); use "
+                      "empc_create");
+    if (!empc::all_finite(A, (size_t)n * n) || !empc::all_finite(B, (size_t)n * m) ||
+        !empc::all_finite(Q, (size_t)n * n) || !empc::all_finite(R, (size_t)m * m))
+        return reject(EMPC_EINVAL, "empc_evaluate_noalloc: non-finite model or weight");
     for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-            if (i != j && Q[(size_t)i * n + j] != 0.0)
-                return (empc_status)set_thread_error(EMPC_EUNSUPPORTED, "Q must be diagonal");
+        if (Q[(size_t)i * n + i] < 0.0) return reject(EMPC_EINVAL, "Q must be >= 0");
     for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j)
-            if (i != j && R[(size_t)i * m + j] != 0.0)
-                return (empc_status)set_thread_error(EMPC_EUNSUPPORTED, "R must be diagonal");
+        if (R[(size_t)i * m + i] < 0.0) return reject(EMPC_EINVAL, "R must be >= 0");
     if (count == 0) return EMPC_OK;
 
     std::lock_guard<std::mutex> lock(g_mutex);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return (empc_status)set_thread_error(EMPC_ECUDA, "empc_evaluate_noalloc: no CUDA device");
+        return reject(EMPC_ECUDA, "empc_evaluate_noalloc: no CUDA device");
     // First call on a device: look up the array's device address with that
     // device current (the host-side symbol is only a stand-in).
     if (!g_dev_tables[dev]) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_eval_tables) != cudaSuccess)
-            return (empc_status)set_thread_error(EMPC_ECUDA, "cudaGetSymbolAddress failed");
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_eval_tables);
+        if (e != cudaSuccess) return reject(EMPC_ECUDA, cudaGetErrorString(e));
         g_dev_tables[dev] = static_cast<float*>(p);
     }
     float* dt = g_dev_tables[dev];
 
-    // Host-side tables, the same construction as empc_create's.
+    // The tables, built by the same code as empc_create's, written straight
+    // into the host staging array at this call's offsets.
+    const bool dense_r = empc::has_off_diagonal(R, m);
+    const bool rotated = empc::has_off_diagonal(Q, n);
+    const Layout L(n, m, horizon, knots, dense_r, rotated);
     float* h = g_host_tables;
-    for (int i = 0; i < n; ++i) {
-        for (int j = 0; j < n; ++j)
-            h[kOffD + i * n + j] = (float)(A[(size_t)i * n + j] - (i == j ? 1.0 : 0.0));
-        h[kOffQ + i] = (float)Q[(size_t)i * n + i];
-        for (int j = 0; j < m; ++j) h[kOffBT + j * n + i] = (float)B[(size_t)i * m + j];
-    }
-    for (int i = 0; i < m; ++i) h[kOffR + i] = (float)R[(size_t)i * m + i];
-    double wd[kMaxKnots] = {0.0}, wo[kMaxKnots] = {0.0};
-    empc::KnotStep* ks = reinterpret_cast<empc::KnotStep*>(h + kOffKnots);
-    const long den = horizon > 1 ? horizon - 1 : 1;
-    for (int k = 0; k < horizon; ++k) {
-        long a = 0, num = 0;
-        if (knots > 1 && horizon > 1) {
-            a = (long)k * (knots - 1) / den;
-            if (a > knots - 2) a = knots - 2;
-            num = (long)k * (knots - 1) - a * den;
-        }
-        const double w1 = (double)num / (double)den, w0 = (double)(den - num) / (double)den;
-        ks[k].idx1 = (int)a;
-        ks[k].w0 = (float)w0;
-        ks[k].w1 = (float)w1;
-        ks[k].pad = 0;
-        wd[a] += w0 * w0;
-        if (knots > 1) {
-            wd[a + 1] += w1 * w1;
-            wo[a] += w0 * w1;
-        }
-    }
-    for (int j = 0; j < knots; ++j) {
-        h[kOffGram + j] = (float)wd[j];
-        h[kOffGram + knots + j] = (float)wo[j];
-    }
+    const empc::TableOut o{h + L.D,
+                           h + L.BT,
+                           h + L.qd,
+                           h + L.rd,
+                           nullptr,
+                           nullptr,
+                           h + L.gram,
+                           reinterpret_cast<empc::KnotStep*>(h + L.ks),
+                           h + L.rmat,
+                           reinterpret_cast<double*>(h + L.Vt),
+                           g_w0,
+                           g_w1,
+                           g_idx,
+                           g_work};
+    bool rot = false, dr = false;
+    const char* msg = "";
+    const empc_status ts = empc::fill_tables(A, B, Q, R, nullptr, n, m, horizon, knots, o, &rot,
+                                             &dr, &msg);
+    if (ts != EMPC_OK) return reject(ts, msg);
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // Pageable source: the copy has been staged when the call returns, so the
     // host tables may be rewritten by the next call.
-    if (cudaMemcpyAsync(dt, h, sizeof(float) * kScratchFloats, cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-        return (empc_status)set_thread_error(EMPC_ECUDA, "table copy failed");
+    cudaError_t e = cudaMemcpyAsync(dt, h, sizeof(float) * L.used, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return reject(EMPC_ECUDA, cudaGetErrorString(e));
 
     empc::RolloutArgs a{};
-    a.D = dt + kOffD;
-    a.BT = dt + kOffBT;
-    a.qdiag = dt + kOffQ;
-    a.rdiag = dt + kOffR;
-    a.gram = dt + kOffGram;
-    a.ktab = reinterpret_cast<const empc::KnotStep*>(dt + kOffKnots);
+    a.D = dt + L.D;
+    a.BT = dt + L.BT;
+    a.qdiag = dt + L.qd;
+    a.rdiag = dt + L.rd;
+    a.rmat = dense_r ? dt + L.rmat : nullptr;
+    a.gram = dt + L.gram;
+    a.ktab = reinterpret_cast<const empc::KnotStep*>(dt + L.ks);
     a.x0 = dev_x0;
     a.goal = dev_goal;
+    if (rotated) {  // start and goal into Q's eigenbasis, inside the array
+        e = empc::launch_rotate(reinterpret_cast<const double*>(dt + L.Vt), dev_x0, dev_goal,
+                                dt + L.zx, dt + L.zg, n, st);
+        if (e != cudaSuccess) return reject(EMPC_ECUDA, cudaGetErrorString(e));
+        a.x0 = dt + L.zx;
+        a.goal = dt + L.zg;
+    }
     a.n = n;
     a.m = m;
     a.T = horizon;
@@ -157,17 +179,19 @@ extern "C" empc_status empc_evaluate_noalloc(const double* A, const double* B, c
     a.pop_in = dev_pop;
     a.cost = dev_cost;
     a.gen = nullptr;
-    // Default tile: warp-synchronous, 2 candidates per thread, 4 warps per CTA.
+    // Tile: warp-synchronous, 2 candidates per thread, 4 warps per CTA when it
+    // fits, else the first shape that fits.
     empc::TileShape shapes[64];
-    const int ns = empc::rollout_shapes(n, shapes, 64);
-    for (int i = 0; i < ns && i < 64; ++i) {
-        const empc::TileShape& s = shapes[i];
-        if (s.kind == 1 && s.cands == 2 && s.groups == 4 &&
-            empc::rollout_shape_supported(s, n, m, knots, horizon))
-            return empc::launch_rollout(a, s, st) == cudaSuccess ? EMPC_OK : EMPC_ECUDA;
-    }
-    for (int i = 0; i < ns && i < 64; ++i)
-        if (empc::rollout_shape_supported(shapes[i], n, m, knots, horizon))
-            return empc::launch_rollout(a, shapes[i], st) == cudaSuccess ? EMPC_OK : EMPC_ECUDA;
-    return EMPC_EUNSUPPORTED;
+    const int ns = std::min(empc::rollout_shapes(n, shapes, 64), 64);
+    int pick = -1;
+    for (int i = 0; i < ns && pick < 0; ++i)
+        if (shapes[i].kind == 1 && shapes[i].cands == 2 && shapes[i].groups == 4 &&
+            empc::rollout_shape_supported(shapes[i], n, m, knots, horizon))
+            pick = i;
+    for (int i = 0; i < ns && pick < 0; ++i)
+        if (empc::rollout_shape_supported(shapes[i], n, m, knots, horizon)) pick = i;
+    if (pick < 0) return reject(EMPC_EUNSUPPORTED, "empc_evaluate_noalloc: no rollout tile fits");
+    e = empc::launch_rollout(a, shapes[pick], st);
+    if (e != cudaSuccess) return reject(EMPC_ECUDA, cudaGetErrorString(e));
+    return EMPC_OK;
 }

@@ -156,6 +156,39 @@ __device__ __forceinline__ void put8(uint8_t* op, int r, int k, const float* v) 
     *reinterpret_cast<uint4*>(op + swz(r, k)) = q;
 }
 
+// Input cost rows i0 .. i1-1 of candidate `cand` for a dense R: sum over
+// those rows of U_i' W y_i, y_i,a = (R U_a)_i (the knots read from the
+// population, coherent with the breeding kernel before this one).  R is
+// symmetric, so row l of R gives column l's weights for every own row.
+__device__ __forceinline__ float input_cost_dense_rows(const RolloutArgs& a, int cand, int i0,
+                                                       int i1) {
+    const int p = a.p, m = a.m;
+    float y[kUW], yp[kUW], up[kUW];
+#pragma unroll
+    for (int r = 0; r < kUW; ++r) yp[r] = up[r] = 0.0f;
+    float s = 0.0f;
+    for (int j = 0; j < p; ++j) {
+#pragma unroll
+        for (int r = 0; r < kUW; ++r) y[r] = 0.0f;
+        for (int l = 0; l < m; ++l) {
+            const float ul = __ldcg(a.pop_in + (size_t)(l * p + j) * a.P + cand);
+#pragma unroll
+            for (int r = 0; r < kUW; ++r)
+                if (i0 + r < i1) y[r] = fmaf(a.rmat[l * m + i0 + r], ul, y[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kUW; ++r) {
+            if (i0 + r >= i1) continue;
+            const float u = __ldcg(a.pop_in + (size_t)((i0 + r) * p + j) * a.P + cand);
+            s = fmaf(a.gram[j] * u, y[r], s);
+            if (j > 0) s = fmaf(a.gram[p + j - 1], fmaf(up[r], y[r], u * yp[r]), s);
+            yp[r] = y[r];
+            up[r] = u;
+        }
+    }
+    return s;
+}
+
 struct Bf16Layout {
     static constexpr int kA0 = 0;                      // A buffer 0
     static constexpr int kA1 = kOperandBytes;          // A buffer 1
@@ -268,7 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
                                                   : 0.0f;
         }
         // segments come in order, each once: W_ss U_s^2 + 2 W_s,s+1 U_s U_s+1,
-        // plus W_{p-1,p-1} U_{p-1}^2 with the last segment
+        // plus W_{p-1,p-1} U_{p-1}^2 with the last segment (diagonal R; a dense
+        // R is taken after the horizon loop)
+        if (a.rmat) return;
         const float wd = a.gram[s];
         const float wo = s + 1 < p ? 2.0f * a.gram[p + s] : 0.0f;
         const float wl = s + 2 == p ? a.gram[s + 1] : 0.0f;
@@ -363,6 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
             if (!mbar_wait(&mbar[g], (uint32_t)(issued & 1))) ok = false;
     }
     if (!ok) abort_sh = 1;
+    if (a.rmat && live) Ju = input_cost_dense_rows(a, cand, i0, min(i0 + kUW, m));
     float jown = Ju;
 #pragma unroll
     for (int j = 0; j < 4; ++j) jown += jacc[j].x + jacc[j].y;

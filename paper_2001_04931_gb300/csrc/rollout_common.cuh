@@ -386,12 +386,32 @@ __device__ void fill_knots(const RolloutArgs& a, float* Us, int xs, int* par, in
 
 // Input cost sum_k u_k' R u_k of one candidate restricted to inputs
 // i0, i0 + istep, ..., in closed form through the tridiagonal Gram matrix of
-// the knot weights (W_aa = gram[a], W_a,a+1 = gram[p + a]).
+// the knot weights (W_aa = gram[a], W_a,a+1 = gram[p + a]):
+// sum_k u_k' R u_k = sum_ij R_ij U_i' W U_j.  Diagonal R: r_i U_i' W U_i.
+// Dense R (a.rmat): row i contributes U_i' W y_i with y_i,a = (R U_a)_i, U_a
+// the inputs' knot a.
 template <class Args>
 __device__ __forceinline__ float input_cost_part(const Args& a, const float* Us, int xs,
                                                  int col, int i0, int istep) {
     const int p = a.p;
     float Ju = 0.0f;
+    if (a.rmat) {
+        for (int i = i0; i < a.m; i += istep) {
+            float s = 0.0f, y_prev = 0.0f, u_prev = 0.0f;
+            for (int j = 0; j < p; ++j) {
+                float y = 0.0f;
+                for (int l = 0; l < a.m; ++l)
+                    y = fmaf(a.rmat[i * a.m + l], Us[(l * p + j) * xs + col], y);
+                const float u = Us[(i * p + j) * xs + col];
+                s = fmaf(a.gram[j] * u, y, s);
+                if (j > 0) s = fmaf(a.gram[p + j - 1], fmaf(u_prev, y, u * y_prev), s);
+                y_prev = y;
+                u_prev = u;
+            }
+            Ju += s;
+        }
+        return Ju;
+    }
     for (int i = i0; i < a.m; i += istep) {
         float s = 0.0f;
         for (int j = 0; j < p; ++j) {

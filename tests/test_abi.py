@@ -64,7 +64,10 @@ def test_zoh_rejects_bad_input(E):
 
 @pytest.mark.parametrize("bad", [
     dict(knots=0), dict(knots=60), dict(horizon=0), dict(pop=0), dict(elite=600),
-    dict(Q=np.ones((4, 4))), dict(R=np.array([[1.0, 0.5], [0.5, 1.0]])),
+    # dense weights are taken, but their symmetric parts must be positive
+    # semidefinite (eigenvalues 3 and -1 here)
+    dict(Q=np.kron(np.eye(2), [[1.0, 2.0], [2.0, 1.0]])), dict(R=np.array([[1.0, 2.0], [2.0, 1.0]])),
+    dict(Q=np.kron(np.eye(2), [[1.0, 4.0], [0.0, 1.0]])),
     dict(bounds=np.array([[1.0, -1.0], [-1.0, 1.0]])), dict(A=np.full((4, 4), np.inf)),
     dict(sigma=-1.0), dict(p_cross_256=300), dict(gate=7), dict(Q=-np.eye(4)),
     dict(evaluator=5), dict(evaluator=1, precision=1), dict(evaluator=1, refine_steps=2),

@@ -53,15 +53,18 @@ __global__ void rollout_block_kernel(const RolloutArgs a) {
     const int cg = tid / nrg;
     pdl_launch_dependents();
 
-    for (int i = tid; i < 2 * NX * xs; i += blockDim.x) {
+    // the initial state and the model tables, with batched loads (none
+    // depends on the previous kernel)
+    batched_fill(X, 2 * NX * xs, tid, blockDim.x, [&](int i) {
         const int k = (i / xs) % NX;
-        X[i] = (i < NX * xs && k < n) ? a.x0[k] : 0.0f;
-    }
-    for (int i = tid; i < m * NX; i += blockDim.x) {
+        return (i < NX * xs && k < n) ? a.x0[k] : 0.0f;
+    });
+    batched_fill(BTs, m * NX, tid, blockDim.x, [&](int i) {
         const int row = i % NX, col = i / NX;
-        BTs[i] = row < n ? a.BT[col * n + row] : 0.0f;
-    }
-    for (int k = tid; k < a.T; k += blockDim.x) ks[k] = a.ktab[k];
+        return row < n ? a.BT[col * n + row] : 0.0f;
+    });
+    batched_fill(reinterpret_cast<float*>(ks), 4 * a.T, tid, blockDim.x,
+                 [&](int i) { return reinterpret_cast<const float*>(a.ktab)[i]; });
     float* Bx = smem + L.off_box;
     const bool hooks = has_hooks(a);
     if (hooks) stage_box(a, Bx, NX, tid, blockDim.x);
@@ -208,7 +211,7 @@ size_t rollout_smem_bytes(const TileShape& s, int n, int m, int p, int T) {
         const int xsw = round_up(cpw, 4);
         const int per_warp = round_up(2 * xr * xsw + m * p * xsw + 2 * xsw, 4);
         const int head = round_up(m * xr, 4) + 4 * T + round_up(n * (s.nx + 2), 4) +
-                         round_up(4 * xr, 4);
+                         round_up(4 * xr, 4) + round_up(xr, 4);
         return sizeof(float) * (size_t)(head + s.groups * per_warp);
     }
     const BlockLayout L(s.nx, s.groups * s.cands, m, p, T);

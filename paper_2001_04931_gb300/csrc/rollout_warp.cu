@@ -38,23 +38,29 @@ __global__ void rollout_warp_kernel(const RolloutArgs a) {
     KnotStep* ks = reinterpret_cast<KnotStep*>(smem + round_up(m * XR, 4));
     float* Ds = smem + round_up(m * XR, 4) + 4 * T;
     float* Bx = Ds + round_up(a.n * DS, 4);
-    float* W = Bx + round_up(4 * XR, 4) + warp * warp_slice_floats<NX, C>(m * a.p);
+    float* X0 = Bx + round_up(4 * XR, 4);
+    float* W = X0 + round_up(XR, 4) + warp * warp_slice_floats<NX, C>(m * a.p);
     const int c0 = a.cand_begin + (blockIdx.x * (blockDim.x >> 5) + warp) * CPW;
     pdl_launch_dependents();
-    for (int i = threadIdx.x; i < m * XR; i += blockDim.x) {
+    // the model tables, staged with batched loads (they do not depend on the
+    // previous kernel, so under programmatic dependent launch this overlaps it)
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    batched_fill(BTs, m * XR, tid, nthr, [&](int i) {
         const int row = i % XR, col = i / XR;
-        BTs[i] = row < a.n ? a.BT[col * a.n + row] : 0.0f;
-    }
-    for (int k = threadIdx.x; k < T; k += blockDim.x) ks[k] = a.ktab[k];
-    for (int i = threadIdx.x; i < a.n * DS; i += blockDim.x) {
-        const int r = i / DS, k = i % DS;
-        Ds[i] = k < a.n ? a.D[r * a.n + k] : 0.0f;
-    }
+        return row < a.n ? a.BT[col * a.n + row] : 0.0f;
+    });
+    batched_fill(reinterpret_cast<float*>(ks), 4 * T, tid, nthr,
+                 [&](int i) { return reinterpret_cast<const float*>(a.ktab)[i]; });
+    batched_fill(Ds, a.n * DS, tid, nthr, [&](int i) {
+        const int r = i / DS, k = i - r * DS;
+        return k < a.n ? a.D[r * a.n + k] : 0.0f;
+    });
+    batched_fill(X0, XR, tid, nthr, [&](int i) { return i < a.n ? a.x0[i] : 0.0f; });
     const bool hooks = has_hooks(a);
-    if (hooks) stage_box(a, Bx, XR, threadIdx.x, blockDim.x);
+    if (hooks) stage_box(a, Bx, XR, tid, nthr);
     __syncthreads();
     if (c0 >= a.P) return;  // no block barrier follows
-    warp_tile<NX, C>(a, c0, W, BTs, ks, Ds, DS, hooks ? Bx : nullptr);
+    warp_tile<NX, C>(a, c0, W, BTs, ks, Ds, DS, hooks ? Bx : nullptr, X0);
 }
 
 template <int NX, int C>

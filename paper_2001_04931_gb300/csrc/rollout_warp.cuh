@@ -119,7 +119,8 @@ template <int NX, int C, bool COHERENT = false>
 __device__ __forceinline__ void warp_tile(const RolloutArgs& a, int c0, float* W,
                                           const float* BTs, const KnotStep* ks,
                                           const float* Ds = nullptr, int ds = 0,
-                                          const float* bx = nullptr) {
+                                          const float* bx = nullptr,
+                                          const float* x0s = nullptr) {
     constexpr int NRG = nrg_of(NX);
     constexpr int R = (NX + NRG - 1) / NRG;
     constexpr int XR = NRG * R;
@@ -134,10 +135,11 @@ __device__ __forceinline__ void warp_tile(const RolloutArgs& a, int c0, float* W
     float* Us = W + 2 * XR * XS;
     int* par = reinterpret_cast<int*>(Us + D * XS);
 
-    for (int i = lane; i < 2 * XR * XS; i += 32) {  // pair-interleaved rows
+    // pair-interleaved rows; x0 from the CTA's staged copy when given
+    for (int i = lane; i < 2 * XR * XS; i += 32) {
         const int j = i % (XR * XS);
         const int k = 2 * (j / (2 * XS)) + (j & 1);
-        X[i] = (i < XR * XS && k < a.n) ? a.x0[k] : 0.0f;
+        X[i] = (i < XR * XS && k < a.n) ? (x0s ? x0s[k] : a.x0[k]) : 0.0f;
     }
     float qd[R], gl[R], xo[R][C], jsum[C];
     float2 d2[R][KP];

@@ -501,16 +501,31 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
                                  "peak": fp32_peak_tf, "unit": "TFLOP/s",
                                  "frac": ep_ach / fp32_peak_tf, "peak_basis": fp32_basis}
     elif condensed:
-        peak, basis, measured = fp32_peak(E, clocks, local_rank)
         D = wl.m * wl.p
-        flops = wl.P * (2 * D * D + 4 * D)  # Y = H U, then U'(Y + g)
-        achieved = flops / (roll_us * 1e-6) / 1e12
-        roof = {"bound": "alu", "kernel": "condensed_kernel (J = U'HU + g'U + c0, FP32)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_basis": basis, "measured_fp32_peak": measured,
-                "frac_of_measured": (achieved / measured) if measured else None,
-                "flops_per_launch": flops, "launch_us": roll_us, "breed_us": breed_us,
-                "select_us": sel_us, "traffic": None}
+        Dp = (D + 63) // 64 * 64
+        if Dp <= 256:  # the tensor-core kernel: Y = U'H in TF32 with head/remainder splits
+            bpeak, bbasis = measured_bf16_peak()
+            peak = bpeak * 1.1 / 2.25
+            flops = wl.P * 2 * D * D  # the contraction, counted once
+            achieved = flops / (roll_us * 1e-6) / 1e12
+            roof = {"bound": "tensor",
+                    "kernel": "condensed_tc_kernel (tcgen05 kind::tf32, Y = U'H, 3 passes)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_basis": f"TF32 = {bbasis} x 1.1/2.25 (nominal dense TF32/BF16 ratio)",
+                    "flops_per_launch": flops, "mma_flops_per_launch": 3 * wl.P * 2 * Dp * Dp,
+                    "launch_us": roll_us, "breed_us": breed_us, "select_us": sel_us,
+                    "traffic": None}
+        else:
+            peak, basis, measured = fp32_peak(E, clocks, local_rank)
+            flops = wl.P * (2 * D * D + 4 * D)  # Y = H U, then U'(Y + g)
+            achieved = flops / (roll_us * 1e-6) / 1e12
+            roof = {"bound": "alu", "kernel": "condensed_kernel (J = U'HU + g'U + c0, FP32)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "peak_basis": basis, "measured_fp32_peak": measured,
+                    "frac_of_measured": (achieved / measured) if measured else None,
+                    "flops_per_launch": flops, "launch_us": roll_us, "breed_us": breed_us,
+                    "select_us": sel_us, "traffic": None}
     else:
         peak, basis, measured = fp32_peak(E, clocks, local_rank)
         flops = alg_flops_per_candidate(wl) * wl.P

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libempc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "rotate.cu", "rollout_block.cu", "rollout_warp.cu", "select.cu", "measure.cu", "noalloc.cu", "grad.cu", "batched.cu", "rollout_bf16.cu", "breed.cu", "condensed.cu"]
+SOURCES = ["api.cu", "rotate.cu", "rollout_block.cu", "rollout_warp.cu", "select.cu", "measure.cu", "noalloc.cu", "grad.cu", "batched.cu", "rollout_bf16.cu", "breed.cu", "condensed.cu", "condensed_tc.cu"]
 
 
 def nvcc() -> str:

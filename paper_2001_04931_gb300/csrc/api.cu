@@ -185,6 +185,9 @@ empc::GradArgs grad_args(empc_handle h) {
 cudaError_t evaluate_population(empc_handle h, const RolloutArgs& a, cudaStream_t st) {
     if (h->cfg.evaluator == EMPC_EVAL_CONDENSED) {
         const empc::CondArgs c{h->Hc, h->gvec, h->c0, a.pop_in, a.cost, h->D, h->Dp, h->P};
+        // the P x D x D product on the tensor cores where D fits one MMA's N
+        if (empc::condensed_tc_supported(h->Dp))
+            return empc::launch_condensed_tc(c, h->status, st, a.pdl != 0);
         return empc::launch_condensed(c, st, a.pdl != 0);
     }
     return empc::launch_rollout(a, h->shape, st);

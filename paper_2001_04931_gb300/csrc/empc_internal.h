@@ -122,6 +122,11 @@ struct CondArgs {
 int condensed_pad(int D);
 bool condensed_supported(int D);
 cudaError_t launch_condensed(const CondArgs& a, cudaStream_t st, bool pdl);
+// The same costs with the product on the tensor cores (condensed_tc.cu):
+// tcgen05 kind::tf32 with head/remainder splits, for padded Dp <= 256;
+// status bit 2 (value 2) reports a bounded wait that gave up.
+bool condensed_tc_supported(int Dp);
+cudaError_t launch_condensed_tc(const CondArgs& a, int* status, cudaStream_t st, bool pdl);
 
 // Fused crossover + mutation (warm) or cold-start draw of candidates
 // cand_begin .. P-1 into pop_out (breed.cu).

@@ -1,5 +1,6 @@
 """Condensed quadratic-form evaluator (Sec. IV-B and IV-E) against the FP64
-oracle.
+oracle: the tensor-core kernel (padded D up to 256) and the CUDA-core one
+(wider D).
 
 The GPU evaluates J(U) = U'HU + g'U + c0 in FP32, with H rounded from the
 host's FP64 Hessian and g, c0 from one FP32 adjoint evaluation at U = 0.  Its
@@ -73,8 +74,9 @@ def _lockstep(wl, generations, seed=5, sample=None):
 @pytest.mark.parametrize("kw", [
     dict(dof=3, T=23, p=4, P=200, E=16),
     dict(dof=2, T=1, p=1, P=33, E=3),
-    dict(dof=5, T=40, p=40, P=70, E=6),
+    dict(dof=5, T=40, p=40, P=70, E=6),     # D = 200: the tensor cores' widest N
     dict(dof=8, T=30, p=7, P=130, E=10),
+    dict(dof=30, T=40, p=10, P=130, E=8),   # D = 300 > 256: the CUDA-core kernel
 ])
 def test_condensed_lockstep_small(kw):
     _lockstep(W.small(**kw), 3)

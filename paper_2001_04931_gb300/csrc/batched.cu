@@ -1,18 +1,22 @@
 // Batched EMPC: many independent problems of uneven size in one persistent
 // launch (no counterpart in the paper, whose GPU runs one problem at a time).
 //
-// Work is a generation-major queue of (problem, candidate tile) items,
-// longest tiles first within a generation.  Every CTA loops: take the next
-// ticket; wait until the item's problem has finished selecting the previous
-// generation; breed and roll out the tile (the warp-synchronous tile of
-// rollout_warp.cuh, reading populations through L2); count the tile done.
-// The CTA that completes a problem's last tile of a generation selects that
-// problem's elites and then publishes the problem as ready for the next
-// generation.  There is no grid-wide barrier: problems advance independently
-// and a CTA only waits when the item it drew belongs to a problem still being
-// selected.  Tickets are taken in generation order by CTAs that are already
-// running, so every wait is for work a running CTA holds: no co-residency of
-// the grid is needed for progress (the grid is sized to fill the GPU once).
+// Work is a generation-major queue of items; within a generation, first the
+// breeding items (problem, candidate chunk), then the rollout items (problem,
+// candidate tile), longest problems first.  Every CTA loops: take the next
+// ticket.  A breeding item waits until its problem has finished selecting the
+// previous generation, then breeds its chunk of candidates with the whole
+// CTA (one thread per candidate and 4-knot group, as the single-problem
+// breeding kernel does) and counts itself done.  A rollout item waits until
+// every breeding item of its problem's generation is done, then rolls out the
+// bred tile (the warp-synchronous tile of rollout_warp.cuh, reading
+// populations through L2) and counts the tile done.  The CTA that completes a
+// problem's last tile of a generation selects that problem's elites and then
+// publishes the problem as ready for the next generation.  There is no
+// grid-wide barrier: problems advance independently.  Every wait is for an
+// item with an earlier ticket, taken by a CTA that is already running and
+// that itself waits only on earlier tickets, so no co-residency of the grid
+// is needed for progress (the grid is sized to fill the GPU once).
 // Waits are bounded by the %globaltimer clock: past the limit the kernel sets
 // an error flag that the host reports as EMPC_ETIMEOUT, and every CTA leaves.
 #include <cuda_runtime.h>
@@ -41,7 +45,12 @@ struct BatchProblem {
     int nx;          // compiled state dimension
     int tiles;       // tiles per generation
     int tile_cands;  // candidates per tile
+    int breeds;      // breeding items per generation
+    int breed_cands; // candidates per breeding item
 };
+
+// Candidates per breeding item.
+constexpr int kBreedChunk = 256;
 
 struct BatchArgs {
     const BatchProblem* probs;
@@ -53,6 +62,7 @@ struct BatchArgs {
     unsigned* ticket;
     unsigned* done;   // tiles completed, per problem (cumulative over generations)
     unsigned* ready;  // generations selected, per problem
+    unsigned* bred;   // breeding items completed, per problem (cumulative)
     int* error;
     int stall_problem;  // fault injection: this problem never publishes (-1: none)
     unsigned long long timeout_ns;
@@ -290,11 +300,17 @@ __global__ void __launch_bounds__(WPC * 32) batched_kernel(const BatchArgs b) {
         const int g = (int)(ticket / (unsigned)b.n_items);
         const int2 it = b.items[ticket % (unsigned)b.n_items];
         const BatchProblem& P = b.probs[it.x];
+        const bool breeding = it.y < 0;
         if (threadIdx.x == 0) {
             int ok = 1;
-            if (g > 0) {
+            // breeding waits for the previous generation's selection, a
+            // rollout tile for all of this generation's breeding
+            const unsigned* ctr = breeding ? b.ready + it.x : b.bred + it.x;
+            const unsigned need =
+                breeding ? (unsigned)g : (unsigned)(g + 1) * (unsigned)P.breeds;
+            if (need > 0) {
                 const unsigned long long t0 = global_ns();
-                while (load_acquire(b.ready + it.x) < (unsigned)g) {
+                while (load_acquire(ctr) < need) {
                     if (*(volatile int*)b.error) {
                         ok = 0;
                         break;
@@ -317,6 +333,34 @@ __global__ void __launch_bounds__(WPC * 32) batched_kernel(const BatchArgs b) {
         a.pop_out = P.pop[b.parity ^ ((g + 1) & 1)];
         a.cand_begin = 0;
         a.pdl = 0;
+        if (breeding) {
+            // candidates [cb, ce) of generation g into pop_out: one thread per
+            // (candidate, 4-knot group), consecutive threads on consecutive
+            // candidates (coalesced stores)
+            const uint32_t gen = *(volatile const uint32_t*)a.gen;
+            const int D = a.m * a.p, nq = (D + 3) >> 2;
+            const int cb = (-1 - it.y) * P.breed_cands;
+            const int nc = min(a.P, cb + P.breed_cands) - cb;
+            for (int w = threadIdx.x; w < nc * nq; w += blockDim.x) {
+                const int c = cb + w % nc, quad = w / nc;
+                int s1 = 0, s2 = -1;
+                if (a.mode == kWarm) parents_of<true>(a, c, gen, s1, s2);
+                float v[4];
+                breed_quad<true>(a, c, quad, gen, s1, s2, v);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (quad * 4 + e < D) a.pop_out[(size_t)(quad * 4 + e) * a.P + c] = v[e];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(b.bred + it.x, 1u);
+            }
+            continue;
+        }
+        // the rollout evaluates the bred population
+        a.mode = kEval;
+        a.pop_in = a.pop_out;
         if (staged != it.x) {
             const int xr = xr_of(P.nx);
             for (int i = threadIdx.x; i < a.m * xr; i += blockDim.x) {
@@ -407,7 +451,7 @@ struct empc_batch_s {
     std::vector<BatchProblem> h_probs;
     int2* d_items[2] = {nullptr, nullptr};
     int n_items[2] = {0, 0};
-    unsigned* d_counters = nullptr;  // ticket | done[count] | ready[count]
+    unsigned* d_counters = nullptr;  // ticket | done[count] | ready[count] | bred[count]
     int* d_error = nullptr;
     float* d_best_knots = nullptr;   // [total_knots]
     float* d_best_costs = nullptr;   // [count]
@@ -470,6 +514,7 @@ BatchArgs batch_args(empc_batch b, int G, bool cold, int parity) {
     a.ticket = b->d_counters;
     a.done = b->d_counters + 1;
     a.ready = b->d_counters + 1 + b->count;
+    a.bred = b->d_counters + 1 + 2 * (size_t)b->count;
     a.error = b->d_error;
     a.stall_problem = b->stall_problem;
     a.timeout_ns = b->timeout_ns;
@@ -490,7 +535,7 @@ size_t batch_smem(empc_batch b, int shape) {
 
 // Enqueue one launch: reset the counters, run G generations.
 cudaError_t enqueue_batch(empc_batch b, int G, bool cold, int parity, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned) * (1 + 2 * (size_t)b->count), st);
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned) * (1 + 3 * (size_t)b->count), st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->d_error, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->d_status, 0, sizeof(int) * (size_t)b->count, st)) != cudaSuccess) return e;
@@ -612,7 +657,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
     const size_t off_best = reserve(b->total_knots);
     const size_t off_bcost = reserve(count);
     const size_t off_bstat = reserve(count);
-    const size_t off_counters = reserve(1 + 2 * (size_t)count);
+    const size_t off_counters = reserve(1 + 3 * (size_t)count);
     const size_t off_error = reserve(1);
     const size_t off_probs = reserve(sizeof(BatchProblem) / 4 * (size_t)count + 4);
     size_t off_items[2];
@@ -627,6 +672,11 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         tcands(empc::kNumBatchShapes, std::vector<int>(count));
     for (int s = 0; s < empc::kNumBatchShapes; ++s) {
         const empc::BatchShape sh = empc::kBatchShapes[s];
+        // a generation: every problem's breeding items, then its rollout tiles
+        for (int i : order) {
+            const int nb = (b->P[i] + empc::kBreedChunk - 1) / empc::kBreedChunk;
+            for (int c = 0; c < nb; ++c) items[s].push_back(make_int2(i, -1 - c));
+        }
         for (int i : order) {
             const int cpt = sh.wpc * (32 / empc::nrg_host(b->nx[i])) * sh.cands;
             const int nt = (b->P[i] + cpt - 1) / cpt;
@@ -742,6 +792,8 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
         bp.best_cost = base + off_bcost + i;
         bp.status = reinterpret_cast<int*>(base + off_bstat + i);
         bp.nx = b->nx[i];
+        bp.breed_cands = empc::kBreedChunk;
+        bp.breeds = (d.pop + empc::kBreedChunk - 1) / empc::kBreedChunk;
     }
     b->d_targets = base + off_tgt;
     b->d_probs = reinterpret_cast<BatchProblem*>(base + off_probs);

@@ -409,12 +409,17 @@ __global__ void __launch_bounds__(WPC * 32) batched_kernel(const BatchArgs b) {
 struct BatchShape {
     int wpc, cands;
 };
-constexpr int kNumBatchShapes = 2;
-constexpr BatchShape kBatchShapes[kNumBatchShapes] = {{4, 2}, {2, 2}};
+constexpr int kNumBatchShapes = 4;
+constexpr BatchShape kBatchShapes[kNumBatchShapes] = {{4, 2}, {2, 2}, {4, 4}, {2, 4}};
 
 using BatchKernel = void (*)(BatchArgs);
 BatchKernel batch_kernel_of(int shape) {
-    return shape == 0 ? batched_kernel<4, 2> : batched_kernel<2, 2>;
+    switch (shape) {
+        case 0: return batched_kernel<4, 2>;
+        case 1: return batched_kernel<2, 2>;
+        case 2: return batched_kernel<4, 4>;
+        default: return batched_kernel<2, 4>;
+    }
 }
 
 int nrg_host(int nx) { return nx == 4 ? 2 : nx == 8 ? 4 : nx <= 24 ? 8 : nx <= 48 ? 16 : 32; }
@@ -449,8 +454,8 @@ struct empc_batch_s {
     char* arena = nullptr;
     BatchProblem* d_probs = nullptr;
     std::vector<BatchProblem> h_probs;
-    int2* d_items[2] = {nullptr, nullptr};
-    int n_items[2] = {0, 0};
+    int2* d_items[empc::kNumBatchShapes] = {};
+    int n_items[empc::kNumBatchShapes] = {};
     unsigned* d_counters = nullptr;  // ticket | done[count] | ready[count] | bred[count]
     int* d_error = nullptr;
     float* d_best_knots = nullptr;   // [total_knots]
@@ -467,7 +472,8 @@ struct empc_batch_s {
     cudaEvent_t tgt_done = nullptr;  // the last targets copy has read h_targets
     int shape = 0, grid = 0;
     size_t smem = 0;
-    int bt_floats = 0, ks_floats = 0, slice_floats[2] = {0, 0}, key_words = 0, sel_cap = 0;
+    int bt_floats = 0, ks_floats = 0, slice_floats[empc::kNumBatchShapes] = {}, key_words = 0,
+        sel_cap = 0;
     int parity = 0;
     bool has_pop = false;
     int stall_problem = -1;
@@ -660,7 +666,7 @@ empc_status empc_batch_create(const empc_problem_desc* probs, int count, const e
     const size_t off_counters = reserve(1 + 3 * (size_t)count);
     const size_t off_error = reserve(1);
     const size_t off_probs = reserve(sizeof(BatchProblem) / 4 * (size_t)count + 4);
-    size_t off_items[2];
+    size_t off_items[empc::kNumBatchShapes];
     // work lists, per launch shape: tiles of each problem, longest first
     std::vector<int> order(count);
     std::iota(order.begin(), order.end(), 0);

@@ -99,3 +99,26 @@ def test_default_config(E):
     assert c.sigma == pytest.approx(0.1) and c.p_cross_256 == 128 and c.p_mutate_256 == 128
     assert c.gate == E.EMPC_GATE_PER_INPUT and c.precision == E.EMPC_FP32
     assert c.evaluator == E.EMPC_EVAL_ROLLOUT
+
+
+def test_batch_create_host_path_without_a_device(E):
+    """empc_batch_create's host work (validation, tables, rotations, the work
+    lists of every launch shape) runs before the first CUDA call: on a host
+    without a GPU it must end in a clean EMPC_ECUDA, never a crash."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present; the GPU tests create batches")
+    except ImportError:
+        pass
+    import workloads as W
+    probs = []
+    for wl in W.batched_problems(64, seed=3):
+        A, B = E.discretize_zoh(wl.plant.Ac, wl.plant.Bc, wl.dt)
+        x0, g = wl.start_goal()
+        probs.append(dict(A=A, B=B, Q=wl.Q(), R=wl.R(), bounds=wl.bounds(), x0=x0, x_goal=g,
+                          horizon=wl.T, knots=wl.p, pop=wl.P, elite=wl.E, seed=wl.seed,
+                          sigma=wl.sigma))
+    with pytest.raises(E.EmpcError) as ei:
+        E.Batch(probs)
+    assert ei.value.status == E.EMPC_ECUDA

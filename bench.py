@@ -428,13 +428,16 @@ def compact(line):
 def run_variants(args, rank, world, local_rank, stream, flush):
     """The other workloads beside the headline one, each timed like it (its
     own warm-up, K timed solves, clock samples) and compared with plain FP32
-    EMPC on the same GPU: c3 (refined), c5 (BF16 tensor cores) and c4 (256
-    problems in one persistent launch)."""
+    EMPC on the same GPU: c3 (refined), c5 (BF16 tensor cores), c4 (256
+    problems in one persistent launch) and c2 with the condensed evaluator
+    (tensor-core product)."""
     import copy
     out = {}
-    for name in ("c3", "c5", "c4"):
+    for name in ("c3", "c5", "c4", "c2_condensed"):
         va = copy.copy(args)
         va.workload, va.tile, va.no_cpu_baseline = name, 0, True
+        if name == "c2_condensed":  # c2 with the condensed quadratic-form evaluator
+            va.workload, va.evaluator = "c2", "condensed"
         va.e2e_steps = min(args.e2e_steps, 10)
         va.compare_seeds = min(args.compare_seeds, 1 if name == "c4" else 3)
         if name == "c4":

@@ -419,7 +419,7 @@ def compact(line):
            "ms_per_step": line["ms_per_step"], "ms_per_problem": line["ms_per_problem"],
            "e2e": line["e2e"], "gpu_launches": line["gpu_launches"], "clocks": line["clocks"],
            "roofline": {k: roof[k] for k in keep if k in roof}}
-    for k in ("compare", "bf16_cost_error"):
+    for k in ("compare", "bf16_cost_error", "adjoint"):
         if k in line:
             out[k] = line[k]
     return out
@@ -550,6 +550,7 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
     if wl.name in ("c3", "c5") and rank == 0:
         compare = compare_variant(E, wl.name, tuple(range(args.compare_seeds)))
     bf16_err = bf16_population_error(prob, wl, x0, g) if bf16 and rank == 0 else None
+    adjoint = adjoint_line(E, prob, wl, stream, clocks, local_rank) if wl.name == "c3" else None
     # per generation: breed, rollout, select (+ the refinement kernel after the first;
     # + one adjoint launch per solve for the condensed terms)
     launches = wl.G * 3 + (wl.G - 1 if wl.name == "c3" else 0) + (1 if condensed else 0)
@@ -575,9 +576,46 @@ def run_single(args, rank, world, local_rank, dist, stream, flush):
         "cpu_baseline": cpu,
         **({"compare": compare} if compare else {}),
         **({"bf16_cost_error": bf16_err} if bf16_err else {}),
+        **({"adjoint": adjoint} if adjoint else {}),
         **({"closed_loop": loop} if loop else {}),
         **({"state_box": box} if box else {}),
     }
+
+
+def adjoint_line(E, prob, wl, stream, clocks, local_rank, reps=10):
+    """The adjoint kernel (empc_grad) on the whole population the last solve
+    left: dJ/dU and J of every candidate in one launch, checkpoints every
+    ckpt_every steps, timed with CUDA events on the handle's stream.
+    Algorithmic FLOPs per candidate: the forward pass T(2n^2 + 6n) + 2pnm,
+    the adjoint recursion T(2n^2 + 4n) (D' lambda, 2 Q e and the sum) and
+    the knot gradient 2pnm + 6mp (B' Lambda and the Gram term); the
+    checkpointed recompute (another forward pass) is overhead, not counted."""
+    import torch
+    pop = torch.empty((prob.D, prob.P), device="cuda")
+    prob.get_state(pop, None, None)
+    grad = torch.empty_like(pop)
+    cost = torch.empty(prob.P, device="cuda")
+    x0, g = wl.start_goal()
+    x0d = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    gd = torch.tensor(g, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            prob.grad(x0d, gd, pop, grad, cost)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            prob.grad(x0d, gd, pop, grad, cost)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    n, m, T, p = wl.n, wl.m, wl.T, wl.p
+    per = T * (2 * n * n + 6 * n) + 2 * p * n * m + T * (2 * n * n + 4 * n) + 2 * p * n * m + 6 * m * p
+    flops = per * prob.P
+    peak, basis, _ = fp32_peak(E, clocks, local_rank)
+    return {"kernel": "grad_warp_kernel (adjoint, checkpoints every %d steps)" % prob.info().ckpt_every,
+            "candidates": prob.P, "launch_us": us, "flops_per_launch": flops,
+            "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / (us * 1e-6) / 1e12 / peak, "peak_basis": basis}
 
 
 def bf16_population_error(prob, wl, x0, g, sample=256):

@@ -77,7 +77,8 @@ struct empc_problem_s {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int ce = 1;            // checkpoint interval
     float eta = 0.0f;      // refinement step
-    int grad_cands = 1, grad_wpc = 2;
+    int grad_cands = 1, grad_wpc = 2;      // adjoint shape for whole populations (empc_grad)
+    int refine_cands = 1, refine_wpc = 2;  // adjoint shape for the elites' refinement
     int grad_nx = 0;  // the adjoint kernel's state class (the warp family's, n <= 64)
     float* sigma_dev = nullptr;  // the mutation sigma the breeding kernel reads
     float sigma_now = 0.0f;      // host copy being transferred to sigma_dev
@@ -238,7 +239,7 @@ cudaError_t enqueue_generation(empc_handle h, bool cold, int parity, cudaStream_
         g.steps = h->cfg.refine_steps;
         if ((e = cudaEventRecord(h->ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0)) != cudaSuccess) return e;
-        e = empc::launch_grad(g, h->grad_nx, h->grad_cands, h->grad_wpc, h->aux_stream);
+        e = empc::launch_grad(g, h->grad_nx, h->refine_cands, h->refine_wpc, h->aux_stream);
         if (e != cudaSuccess) return e;
         if ((e = cudaEventRecord(h->ev_join, h->aux_stream)) != cudaSuccess) return e;
     }
@@ -480,6 +481,86 @@ empc_status autotune(empc_handle h) {
     EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
     h->shape = best_s;
     h->tuned_us = best * 1000.0f;
+    return EMPC_OK;
+}
+
+// Adjoint kernel shapes (candidates per lane 1 or 2, warps per CTA 4, 2 or
+// 1, within shared memory), each timed on the cold population the rollout
+// autotuner drew: the gradient of the whole population (empc_grad) and, with
+// refinement on, the refinement of E elites.  The per-candidate arithmetic
+// does not depend on the shape.  Leaves grad_wpc = 0 when no shape fits.
+empc_status autotune_grad(empc_handle h) {
+    struct Shape {
+        int cands, wpc;
+    };
+    std::vector<Shape> ok;
+    for (int c : {1, 2})
+        for (int wpc : {4, 2, 1})
+            if (empc::grad_smem_bytes(h->grad_nx, empc::warp_nrg(h->grad_nx), c, wpc, h->n, h->m,
+                                      h->p, h->T, h->ce) <= 227u * 1024u)
+                ok.push_back(Shape{c, wpc});
+    h->grad_wpc = h->refine_wpc = 0;
+    if (ok.empty()) return EMPC_OK;
+    cudaEvent_t e0, e1;
+    EMPC_CUDA(h, cudaEventCreate(&e0));
+    EMPC_CUDA(h, cudaEventCreate(&e1));
+    auto time_shape = [&](const Shape& sh, bool refine) {
+        empc::GradArgs g = grad_args(h);
+        g.pop_in = h->pop[0];
+        g.ld_in = h->P;
+        g.cost = h->cost;
+        if (refine) {  // E elites (the first E columns), written to the spare buffer
+            g.count = h->E;
+            g.pop_out = h->pop[1];
+            g.ld_out = h->P;
+            g.steps = h->cfg.refine_steps;
+        } else {  // the gradient of every candidate, into the spare buffer
+            g.count = h->P;
+            g.grad = h->pop[1];
+            g.ld_grad = h->P;
+            g.steps = 0;
+        }
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            const cudaError_t e = empc::launch_grad(g, h->grad_nx, sh.cands, sh.wpc, h->stream);
+            cudaEventRecord(e1, h->stream);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                return 1e30f;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    float bg = 1e30f, br = 1e30f;
+    for (const Shape& sh : ok) {
+        const float tg = time_shape(sh, false);
+        if (tg < bg) {
+            bg = tg;
+            h->grad_cands = sh.cands;
+            h->grad_wpc = sh.wpc;
+        }
+        if (h->cfg.refine_steps > 0) {
+            const float tr = time_shape(sh, true);
+            if (tr < br) {
+                br = tr;
+                h->refine_cands = sh.cands;
+                h->refine_wpc = sh.wpc;
+            }
+        }
+    }
+    if (h->cfg.refine_steps <= 0) {
+        h->refine_cands = h->grad_cands;
+        h->refine_wpc = h->grad_wpc;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->grad_wpc == 0 || h->refine_wpc == 0)
+        return fail(h, EMPC_ECUDA, "no adjoint kernel shape ran");
     return EMPC_OK;
 }
 
@@ -782,20 +863,9 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
 #undef EMPC_TRY
     empc_status s = autotune(h);
     if (s == EMPC_OK && h->n <= 64) {
-        // adjoint kernel shape: 1 candidate per lane, the most warps per CTA
-        // whose shared memory fits
-        h->grad_cands = 1;
-        h->grad_wpc = 0;
         h->grad_nx = empc::warp_class_nx(n);
-        for (int wpc : {4, 2, 1}) {
-            const size_t need = empc::grad_smem_bytes(h->grad_nx, empc::warp_nrg(h->grad_nx), 1,
-                                                      wpc, n, m, knots, horizon, h->ce);
-            if (need <= 227u * 1024u) {
-                h->grad_wpc = wpc;
-                break;
-            }
-        }
-        if (h->grad_wpc == 0 && cfg.refine_steps > 0)
+        s = autotune_grad(h);
+        if (s == EMPC_OK && h->grad_wpc == 0 && cfg.refine_steps > 0)
             s = fail(h, EMPC_EUNSUPPORTED, "adjoint checkpoints do not fit in shared memory");
     }
     if (s != EMPC_OK) {

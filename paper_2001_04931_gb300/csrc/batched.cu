@@ -558,7 +558,12 @@ empc_status configure_shape(empc_batch b, int shape) {
     auto kern = empc::batch_kernel_of(shape);
     const size_t smem = batch_smem(b, shape);
     if (smem > 227u * 1024u) return bfail(b, EMPC_EUNSUPPORTED, "batch does not fit in shared memory");
-    EMPC_BCUDA(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // raise the kernel's limit on this device, never lower it: another batch
+    // on the device may launch the same kernel with more shared memory
+    cudaFuncAttributes fa{};
+    EMPC_BCUDA(b, cudaFuncGetAttributes(&fa, kern));
+    if ((int)smem > fa.maxDynamicSharedSizeBytes)
+        EMPC_BCUDA(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     EMPC_BCUDA(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                       &per_sm, kern, 32 * empc::kBatchShapes[shape].wpc, smem));

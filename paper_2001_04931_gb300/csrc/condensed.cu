@@ -121,13 +121,8 @@ cudaError_t launch_tile(const CondArgs& a, cudaStream_t st, bool pdl) {
     constexpr int NCT = TC * MC;
     const size_t smem = sizeof(float) * ((size_t)a.Dp * NCT + kJC * TI * MI + TI * NCT);
     auto kern = condensed_kernel<TI, TC, MI, MC>;
-    static int smem_cap = 48 * 1024;
-    if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_cap = (int)smem;
-    }
+    static int smem_cap[kMaxDevices] = {};
+    if (cudaError_t e = raise_smem_limit(kern, smem, smem_cap); e != cudaSuccess) return e;
     const int grid = (a.P + NCT - 1) / NCT;
     return launch_kernel(kern, dim3(grid), dim3(TI * TC), smem, st, pdl, a);
 }

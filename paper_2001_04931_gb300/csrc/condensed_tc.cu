@@ -281,13 +281,8 @@ cudaError_t launch_condensed_tc(const CondArgs& a, int* status, cudaStream_t st,
     if (a.P <= 0) return cudaSuccess;
     const size_t smem = condensed_tc_smem_bytes(a.Dp);
     if (smem > 227u * 1024u) return cudaErrorInvalidValue;
-    static int smem_cap = 48 * 1024;
-    if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(condensed_tc_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_cap = (int)smem;
-    }
+    static int smem_cap[kMaxDevices] = {};
+    if (cudaError_t e = raise_smem_limit(condensed_tc_kernel, smem, smem_cap); e != cudaSuccess) return e;
     const int grid = (a.P + kM - 1) / kM;
     return launch_kernel(condensed_tc_kernel, dim3(grid), dim3(kThreadsTC), smem, st, pdl, a,
                          status);

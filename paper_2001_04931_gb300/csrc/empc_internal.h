@@ -77,6 +77,24 @@ cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Dynamic shared memory above 48 KiB needs the kernel's limit raised, and the
+// limit is kept per device: cap[d] records what was set on device d (zero:
+// nothing yet).  The attribute call is made only when the need grows, so a
+// launch recorded into a CUDA graph after the first one makes none.
+constexpr int kMaxDevices = 64;
+template <typename Kern>
+cudaError_t raise_smem_limit(Kern kern, size_t smem, int (&cap)[kMaxDevices]) {
+    if (smem <= 48u * 1024u) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if ((int)smem <= cap[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cap[dev] = (int)smem;
+    return e;
+}
+
 // Adjoint-gradient / refinement kernel arguments (grad.cu).
 struct GradArgs {
     const float* D;

@@ -397,13 +397,8 @@ cudaError_t launch_grad_shape(const GradArgs& a, int wpc, cudaStream_t st) {
     constexpr int NRG = NX == 4 ? 2 : NX == 8 ? 4 : NX <= 24 ? 8 : NX <= 48 ? 16 : 32;
     const size_t smem = grad_smem_bytes(NX, NRG, C, wpc, a.n, a.m, a.p, a.T, a.ce);
     auto kern = grad_warp_kernel<NX, NRG, C>;
-    static int smem_cap = 48 * 1024;
-    if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_cap = (int)smem;
-    }
+    static int smem_cap[kMaxDevices] = {};
+    if (cudaError_t e = raise_smem_limit(kern, smem, smem_cap); e != cudaSuccess) return e;
     constexpr int CPW = (32 / NRG) * C;
     const int per_cta = wpc * CPW;
     const int grid = (a.count + per_cta - 1) / per_cta;

@@ -433,13 +433,8 @@ template <int NG>
 cudaError_t launch_groups(const RolloutArgs& a, cudaStream_t st) {
     auto kern = rollout_bf16_kernel<NG>;
     const size_t smem = rollout_bf16_smem_bytes(a.T);
-    static int smem_cap = 48 * 1024;
-    if ((int)smem > smem_cap) {
-        cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_cap = (int)smem;
-    }
+    static int smem_cap[kMaxDevices] = {};
+    if (cudaError_t e = raise_smem_limit(kern, smem, smem_cap); e != cudaSuccess) return e;
     const int grid = (a.P - a.cand_begin + kTileCands - 1) / kTileCands;
     if (grid <= 0) return cudaSuccess;
     return launch_kernel(kern, dim3(grid), dim3(kThreads), smem, st, a.pdl != 0, a);

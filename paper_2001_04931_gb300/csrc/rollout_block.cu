@@ -102,15 +102,8 @@ cudaError_t launch_shape(const RolloutArgs& a, int groups, cudaStream_t st) {
     const BlockLayout L(NX, ptile, a.m, a.p, a.T);
     const size_t smem = sizeof(float) * (size_t)L.total;
     auto kern = rollout_block_kernel<NX, R, C>;
-    // Raise the dynamic shared-memory cap only when it grows, so that launches
-    // recorded into a CUDA graph make no attribute calls.
-    static int smem_cap = 48 * 1024;
-    if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_cap = (int)smem;
-    }
+    static int smem_cap[kMaxDevices] = {};
+    if (cudaError_t e = raise_smem_limit(kern, smem, smem_cap); e != cudaSuccess) return e;
     const int grid = (a.P - a.cand_begin + ptile - 1) / ptile;
     if (grid <= 0) return cudaSuccess;
     return launch_kernel(kern, dim3(grid), dim3(nrg * groups), smem, st, a.pdl != 0, a);

@@ -70,13 +70,8 @@ cudaError_t launch_shape(const RolloutArgs& a, int wpc, cudaStream_t st) {
     TileShape s{1, NX, (NX + NRG - 1) / NRG, C, wpc};
     const size_t smem = rollout_smem_bytes(s, a.n, a.m, a.p, a.T);
     auto kern = rollout_warp_kernel<NX, C>;
-    static int smem_cap = 48 * 1024;
-    if ((int)smem > smem_cap) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        smem_cap = (int)smem;
-    }
+    static int smem_cap[kMaxDevices] = {};
+    if (cudaError_t e = raise_smem_limit(kern, smem, smem_cap); e != cudaSuccess) return e;
     const int per_cta = wpc * CPW;
     const int grid = (a.P - a.cand_begin + per_cta - 1) / per_cta;
     if (grid <= 0) return cudaSuccess;

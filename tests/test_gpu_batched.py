@@ -129,3 +129,20 @@ def test_batched_new_targets_warm_start_matches_single_problems():
         bt.set_targets(bad, g1)
     assert ei.value.status == E.EMPC_EINVAL
     bt.close()
+
+
+def test_a_second_batch_does_not_lower_the_first_ones_shared_memory_limit():
+    # Both batches use the same launch shape; the first needs more than 48 KiB
+    # of shared memory (its 8192-candidate key array alone is 32 KiB), the
+    # second much less.  Configuring the second must leave the kernel's limit
+    # high enough for the first to keep launching.
+    import paper_2001_04931_gb300 as E
+    big = E.Batch(_problems([W.small(name="big", seed=1, dof=2, T=20, p=3, P=8192, E=64)]),
+                  tile=1)
+    small = E.Batch(_problems([W.small(name="small", seed=2, dof=2, T=20, p=3, P=64, E=4)]),
+                    tile=1)
+    _, c_small = small.solve(2)
+    _, c_big = big.solve(2)
+    assert np.isfinite(c_small).all() and np.isfinite(c_big).all()
+    big.close()
+    small.close()

@@ -238,6 +238,44 @@ def test_warm_start_persists_and_reset_starts_cold():
     prob.close()
 
 
+def _same_state(a, b):
+    for x, y in zip(_state(a), _state(b)):
+        np.testing.assert_array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+@pytest.mark.parametrize("case", ["ragged", "gate1", "c2", "condensed"])
+def test_multi_generation_solve_equals_single_generation_solves(case):
+    # One captured graph of G generations against G graphs of one generation
+    # (each of which the lockstep tests check against the oracle): the same
+    # populations, costs, elites, best plan and generation counter, bit for
+    # bit, from a cold start and again from the warm start that follows.
+    import paper_2001_04931_gb300 as E
+    cfg = {}
+    if case == "ragged":
+        wl = W.small(dof=3, T=23, p=4, P=200, E=16)
+    elif case == "gate1":
+        wl = W.small(dof=2, T=17, p=3, P=96, E=8, sigma=0.3)
+        cfg = {"gate": 1}
+    elif case == "c2":
+        wl = W.config("c2")
+    else:
+        wl = W.small(dof=3, T=30, p=4, P=700, E=32)
+        cfg = {"evaluator": E.EMPC_EVAL_CONDENSED}
+    x0, g = wl.start_goal()
+    a = gpu_problem(wl, seed=6, **cfg)
+    b = gpu_problem(wl, seed=6, **cfg)
+    for G in (4, 3):
+        ka, ca = a.solve(x0, g, G)
+        for _ in range(G):
+            kb, cb = b.solve(x0, g, 1)
+        np.testing.assert_array_equal(ka.view(np.uint32), kb.view(np.uint32))
+        assert np.float32(ca).view(np.uint32) == np.float32(cb).view(np.uint32)
+        assert a.info().generation == b.info().generation
+        _same_state(a, b)
+    a.close()
+    b.close()
+
+
 def test_solve_device_matches_host_solve():
     torch = _torch()
     wl = W.small(dof=3, T=25, p=4, P=256, E=16)

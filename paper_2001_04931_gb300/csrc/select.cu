@@ -6,8 +6,9 @@
 // with its index into a unique 64-bit (key, index) word.  The kernel picks a
 // threshold key tau with at least E and at most 2048 words whose keys are at
 // most tau, compacts those words into shared memory and ranks them: by
-// counting when there are at most 256, else by sorting 64-word chunks (one
-// warp each, register shuffles) and binary-searching the other chunks.
+// counting when there are at most 256 (two or four lanes per word), else by
+// sorting 64-word chunks (one warp each, register shuffles) and
+// binary-searching the other chunks.
 // Thresholds tried, in order:
 //   1. the words of sixteen of the slots 0..E-1 (after a warm start those
 //      slots hold the previous elites in rank order, so one of them usually
@@ -17,8 +18,9 @@
 //      expected E/P quantile;
 //   3. an exact radix select (8 bits per pass, warp-aggregated shared
 //      histogram) of the E-th smallest word.
-// Then the best candidate's knots and cost are copied out and the generation
-// counter that keys the next generation's draws is bumped.
+// The best candidate's knots are copied out while the words are ranked; the
+// elite and best costs are decoded from the keys; the generation counter that
+// keys the next generation's draws is advanced.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -64,20 +66,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return r;
 }
 
-// Copy the best candidate's knots and cost out; bump the generation counter.
-__device__ __forceinline__ void finish_select(const float* cost, int P,
-                                              const float* pop, int D,
-                                              float* best_knots,
-                                              float* best_cost,
-                                              uint32_t* gen,
-                                              int* status, int best) {
-    for (int q = threadIdx.x; q < D; q += blockDim.x) best_knots[q] = __ldcg(pop + (size_t)q * P + best);
-    if (threadIdx.x == 0) {
-        const float bc = __ldcg(cost + best);
-        *best_cost = bc;
-        if (gen) *gen += 1u;
-        if (status && !(bc < __int_as_float(0x7f800000))) atomicOr(status, 1);
-    }
+// The cost a key was made from: exact for every finite or infinite cost.  A
+// NaN cost was keyed as +inf, so a caller that decodes +inf re-reads the cost.
+__device__ __forceinline__ float key_cost(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
 // One compare-exchange of a bitonic network, seen from the element at
@@ -175,7 +167,6 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
     __shared__ uint32_t warp_tot[32];
     __shared__ uint32_t s_digit, s_rem;
     __shared__ uint32_t s_count;
-    __shared__ unsigned long long s_red64[32];
     __shared__ unsigned long long sel[kMaxElite];
 
     const int tid = threadIdx.x;
@@ -184,6 +175,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
     // the costs come from the kernel this one may overlap: every read of them
     // below is a coherent (L2) load issued after the wait
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    const uint32_t gen0 = (tid == 0 && gen) ? *gen : 0u;  // advanced at the end
     constexpr unsigned long long kNone = ~0ull;
     unsigned long long w[KPT];  // (key, index); kNone past P
 #pragma unroll
@@ -194,42 +186,38 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
     }
 
     // ---- 1. thresholds from the slots 0..E-1: sixteen slot words and K*
+    // Thread i < 16 reads threshold i's slot itself, so the slot keys, the
+    // per-warp maxima of slots 0..E-1 and the zeroed totals need one barrier
+    // before the counting, and the warp counts one more before the choice.
     constexpr int kThr = 16;
-    __shared__ uint32_t s_thr[kThr + 1];
-    __shared__ uint32_t s_cnt[32][kThr + 1];
+    __shared__ uint32_t s_thr[kThr];
+    __shared__ uint32_t s_kmax[32];
+    __shared__ uint32_t s_tot[kThr + 1];
     uint32_t tau;  // threshold key: the words with keys at most tau are ranked
     uint32_t L;
     {
-        if (tid < kThr) s_thr[tid] = 0u;  // a threshold no slot supplies bounds nothing
-        __syncthreads();
-        unsigned long long kmax = 0ull;
-#pragma unroll
-        for (int j = 0; j < KPT; ++j) {
-            const int idx = tid * KPT + j;
-            if (idx < E) {
-                kmax = max(kmax, w[j]);
-                // slot (i+1) E / kThr - 1 supplies threshold i
-                const int i = (kThr * (idx + 1) + E - 1) / E - 1;
-                if (i >= 0 && i < kThr && idx == (i + 1) * E / kThr - 1)
-                    s_thr[i] = (uint32_t)(w[j] >> 32);
-            }
+        if (tid < kThr) {
+            // slot (i+1) E / kThr - 1 supplies threshold i; a threshold no slot
+            // supplies bounds nothing
+            const int slot = (tid + 1) * E / kThr - 1;
+            s_thr[tid] = slot >= 0 ? order_key(__ldcg(cost + slot)) : 0u;
         }
+        if (tid <= kThr) s_tot[tid] = 0u;
+        uint32_t kmax = 0u;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-        if (lane == 0) s_red64[warp] = kmax;
+        for (int j = 0; j < KPT; ++j)
+            if (tid * KPT + j < E) kmax = max(kmax, (uint32_t)(w[j] >> 32));
+        kmax = __reduce_max_sync(0xffffffffu, kmax);
+        if (lane == 0) s_kmax[warp] = kmax;
         __syncthreads();
-        if (tid == 0) {
-            unsigned long long v = 0ull;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v = max(v, s_red64[w2]);
-            s_thr[kThr] = (uint32_t)(v >> 32);
-        }
-        __syncthreads();
+        uint32_t thr[kThr + 1];
+#pragma unroll
+        for (int i = 0; i < kThr; ++i) thr[i] = s_thr[i];
+        thr[kThr] = 0u;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) thr[kThr] = max(thr[kThr], s_kmax[w2]);
         uint32_t c[kThr + 1];
 #pragma unroll
         for (int i = 0; i <= kThr; ++i) c[i] = 0;
-        uint32_t thr[kThr + 1];
-#pragma unroll
-        for (int i = 0; i <= kThr; ++i) thr[i] = s_thr[i];
 #pragma unroll
         for (int j = 0; j < KPT; ++j) {
             const uint32_t kj = (uint32_t)(w[j] >> 32);
@@ -239,24 +227,18 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
 #pragma unroll
         for (int i = 0; i <= kThr; ++i) {
             c[i] = __reduce_add_sync(0xffffffffu, c[i]);
-            if (lane == 0) s_cnt[warp][i] = c[i];
-        }
-        __syncthreads();
-        if (tid <= kThr) {
-            uint32_t sum = 0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) sum += s_cnt[w2][tid];
-            s_cnt[0][tid] = sum;  // row 0 of column tid is read above by this thread only
+            if (lane == 0) atomicAdd(&s_tot[i], c[i]);
         }
         __syncthreads();
         // the threshold bounding the fewest words, but at least E (K* always does)
-        tau = s_thr[kThr];
-        L = s_cnt[0][kThr];
+        tau = thr[kThr];
+        L = s_tot[kThr];
 #pragma unroll
         for (int i = 0; i < kThr; ++i) {
-            const uint32_t ci = s_cnt[0][i];
+            const uint32_t ci = s_tot[i];
             if (ci >= (uint32_t)E && ci < L) {
                 L = ci;
-                tau = s_thr[i];
+                tau = thr[i];
             }
         }
     }
@@ -373,29 +355,52 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
         L = (uint32_t)E;
     }
     __syncthreads();
-    __shared__ int s_best;
+    // The best word (rank 0): every warp finds it, so the best plan's loads
+    // are in flight while the words are ranked.
+    unsigned long long bw = kNone;
+    for (int f = lane; f < (int)L; f += 32) bw = min(bw, sel[f]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bw = min(bw, __shfl_xor_sync(0xffffffffu, bw, o));
+    const int best = (int)(bw & 0xFFFFFFFFull);
+    // issued now, stored after the ranking: a store would wait for its load
+    const float bk0 = tid < D ? __ldcg(pop + (size_t)tid * P + best) : 0.0f;
+    const float kInf = __int_as_float(0x7f800000);
     auto keep = [&](int rank, unsigned long long x) {
         if (rank < E) {
             const int idx = (int)(x & 0xFFFFFFFFull);
+            float c = key_cost((uint32_t)(x >> 32));
+            if (c == kInf) c = __ldcg(cost + idx);  // +inf or NaN
             elite_idx[rank] = idx;
-            elite_cost[rank] = __ldcg(cost + idx);
-            if (rank == 0) s_best = idx;
+            elite_cost[rank] = c;
         }
     };
     if (L <= 256u) {
-        // few words: one thread ranks each by counting the words below it
-        // (every thread reads the same word in each iteration: a broadcast)
-        if (tid < (int)L) {
-            const unsigned long long mine = sel[tid];
+        // few words: S adjacent lanes rank each word by counting the words
+        // below it, each over a 1/S share of them (every lane of a group reads
+        // the same word in each iteration: a broadcast), then add up their counts
+        const int S = L <= 128u ? 4 : 2;
+        const int e = tid / S, part = tid % S;
+        if (warp * 32 / S < (int)L) {  // warp-uniform: the warp holds a word
+            const int f0 = part * (int)L / S, f1 = (part + 1) * (int)L / S;
+            const unsigned long long mine = e < (int)L ? sel[e] : kNone;
             int rank = 0;
-            for (int f = 0; f < (int)L; ++f) rank += sel[f] < mine;
-            keep(rank, mine);
+            for (int f = f0; f < f1; ++f) rank += sel[f] < mine;
+            for (int o = 1; o < S; o <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+            if (part == 0 && e < (int)L) keep(rank, mine);
         }
     } else {
         rank_words(sel, (int)L, keep);
     }
-    __syncthreads();
-    finish_select(cost, P, pop, D, best_knots, best_cost, gen, status, s_best);
+    if (tid < D) best_knots[tid] = bk0;
+    for (int q = tid + (int)blockDim.x; q < D; q += blockDim.x)
+        best_knots[q] = __ldcg(pop + (size_t)q * P + best);
+    if (tid == 0) {
+        float bc = key_cost((uint32_t)(bw >> 32));
+        if (bc == kInf) bc = __ldcg(cost + best);
+        *best_cost = bc;
+        if (gen) *gen = gen0 + 1u;
+        if (status && !(bc < kInf)) atomicOr(status, 1);
+    }
 }
 
 }  // namespace

@@ -14,7 +14,8 @@
 //      slots hold the previous elites in rank order, so one of them usually
 //      bounds a little more than E words), and K*, the largest word of those
 //      slots (which always bounds at least E);
-//   2. a quantile of a sorted stride sample of the words, a little above the
+//   2. when those bound more than 2048 words, or more than 4 E + 256, a
+//      quantile of a sorted stride sample of the words, a little above the
 //      expected E/P quantile;
 //   3. an exact radix select (8 bits per pass, warp-aggregated shared
 //      histogram) of the E-th smallest word.
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
             s_thr[tid] = slot >= 0 ? order_key(__ldcg(cost + slot)) : 0u;
         }
         if (tid <= kThr) s_tot[tid] = 0u;
+        if (tid == 0) s_count = 0u;  // the compaction's reservations
         uint32_t kmax = 0u;
 #pragma unroll
         for (int j = 0; j < KPT; ++j)
@@ -243,8 +245,9 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
         }
     }
 
-    // ---- 2. a sample quantile when none of them admits at most 2048
-    if (L > (uint32_t)kMaxElite) {
+    // ---- 2. a sample quantile when none of them admits at most 2048, or
+    // admits many more words than E (ranking a 512-word sample costs less)
+    if (L > (uint32_t)kMaxElite || L > 4u * (uint32_t)E + 256u) {
         const int S = min((int)blockDim.x, (P + KPT - 1) / KPT);  // threads holding a word
         __shared__ uint32_t s_ts;
         sel[tid] = tid < S ? w[0] : kNone;                        // stride-KPT sample
@@ -255,24 +258,34 @@ __global__ void __launch_bounds__(kSelThreads, 1) select_kernel(
         __syncthreads();
         const uint32_t ts = s_ts;
         const uint32_t Ls = count_at_most<KPT>(w, ts, warp_tot);
-        if (Ls >= (uint32_t)E && Ls <= (uint32_t)kMaxElite) {
+        if (Ls >= (uint32_t)E && Ls < L && Ls <= (uint32_t)kMaxElite) {
             tau = ts;
             L = Ls;
         }
     }
 
     if (L <= (uint32_t)kMaxElite) {
-        // ---- compact the words at or below tau, sort, keep the first E
-        if (tid == 0) s_count = 0;
-        __syncthreads();
+        // ---- compact the words at or below tau, sort, keep the first E: one
+        // reservation per warp for up to 16 of its words each (s_count was
+        // zeroed before the threshold phase's first barrier)
+        constexpr int kG = KPT < 16 ? KPT : 16;
+        const uint32_t below = (1u << lane) - 1u;
 #pragma unroll
-        for (int j = 0; j < KPT; ++j) {
-            const bool take = (uint32_t)(w[j] >> 32) <= tau;
-            const uint32_t ball = __ballot_sync(0xffffffffu, take);
+        for (int j0 = 0; j0 < KPT; j0 += kG) {
+            uint32_t ball[kG], tot = 0;
+#pragma unroll
+            for (int j = 0; j < kG; ++j) {
+                ball[j] = __ballot_sync(0xffffffffu, (uint32_t)(w[j0 + j] >> 32) <= tau);
+                tot += (uint32_t)__popc(ball[j]);
+            }
             uint32_t base = 0;
-            if (lane == 0 && ball) base = atomicAdd(&s_count, (uint32_t)__popc(ball));
+            if (lane == 0 && tot) base = atomicAdd(&s_count, tot);
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) sel[base + __popc(ball & ((1u << lane) - 1u))] = w[j];
+#pragma unroll
+            for (int j = 0; j < kG; ++j) {
+                if ((ball[j] >> lane) & 1u) sel[base + __popc(ball[j] & below)] = w[j0 + j];
+                base += (uint32_t)__popc(ball[j]);
+            }
         }
     } else {
         // ---- 3. exact radix select of the E-th smallest key

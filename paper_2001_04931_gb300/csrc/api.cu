@@ -411,8 +411,8 @@ empc_status run_generations(empc_handle h, int G) {
 empc_status autotune(empc_handle h) {
     std::vector<TileShape> ok;
     if (h->cfg.precision == EMPC_BF16) {
-        // tensor-core tile: the product issued as 1, 2 or 4 MMA groups
-        for (int g : {1, 2, 4}) ok.push_back(TileShape{2, 128, 1, 1, g});
+        // tensor-core tile: 128 candidates, one shape
+        ok.push_back(TileShape{2, 128, 1, 1, 1});
     } else {
         TileShape buf[128];
         const int ns = std::min(empc::rollout_shapes(h->n, buf, 128), 128);

@@ -152,7 +152,7 @@ cudaError_t launch_breed(const RolloutArgs& a, cudaStream_t st);
 
 // BF16 tensor-core rollout (rollout_bf16.cu): n <= 128, m <= 64.
 // The product in `groups` (1, 2 or 4) MMA groups; evaluates pop_in (kEval).
-cudaError_t launch_rollout_bf16(const RolloutArgs& a, int groups, cudaStream_t st);
+cudaError_t launch_rollout_bf16(const RolloutArgs& a, cudaStream_t st);
 bool rollout_bf16_supported(int n, int m, int T);
 size_t rollout_bf16_smem_bytes(int T);
 int rollout_bf16_threads();

@@ -5,27 +5,36 @@
 // For a tile of 128 candidates the step x_{k+1} = x_k + D x_k + B_d u_k
 // (D = A_d - I, Eq. first_order_integration in delta form) is one
 // 128 x 128 x 192 contraction per step, accumulated onto the state itself:
-//   X[c][i] += sum_{k<128} x_c[k] D[i][k] + sum_{j<64} u_c[j] B_d[i][j],
-// with A = [x_c | u_c] (candidates x K, BF16) and B = [D | B_d] (states x K,
-// BF16, constant), both K-major with the 128-byte swizzle in shared memory.
+//   X[c][i] += sum_{j<64} u_c[j] B_d[i][j] + sum_{k<128} x_c[k] D[i][k].
 // The FP32 state X lives in tensor memory for the whole horizon (TMEM lane =
-// candidate, column = state): the MMA adds the increment to it, so no thread
-// keeps or updates a master copy.  Each step runs as four N = 32 column
-// chunks of threads; the product is issued as NG MMA groups of N = 128 / NG
-// columns (NG = 1, 2 or 4, chosen by the autotuner), each committed to its
-// own mbarrier, and the 512 threads are (chunk, candidate) pairs.  A thread waits for its chunk, reads its 32 states of
-// x_{k+1}, accumulates their stage cost (x_{k+1}-g)' Q (x_{k+1}-g), rounds
-// them to BF16 into the next step's A row, and writes its 16 inputs of
-// u_{k+1} (knots kept in registers per segment).  A is double-buffered, so
-// the early chunks' epilogues overlap the later chunks' MMAs.  The input cost
-// sum_k u_k' R u_k is added in closed form from the knots (Gram of the knot
-// weights), in FP32.
+// candidate, column = state): the MMAs add the increment to it, so no thread
+// keeps or updates a master copy.  The A operand, [u_c | x_c] in BF16, lives
+// in tensor memory too (two BF16 per 32-bit column, lane = candidate), so the
+// MMAs read only the constant B = [B_d | D] (states x K, K-major, 128-byte
+// swizzle) from shared memory, and the epilogue writes its BF16 state with
+// tcgen05.st instead of shared-memory stores.
+//
+// Roles.  One thread of a 17th warp issues every MMA.  The 512 threads of
+// the other 16 warps are (32-state chunk, candidate) pairs; per step each
+//   1. writes its 16 inputs of u_{k+1} (the segment's knots parked in tensor
+//      memory) into the spare input buffer while step k's MMAs run,
+//   2. waits for step k's MMAs, reads its 32 states of x_{k+1} from X, and
+//      signals "X read": the issuer starts step k+1 with the input MMAs
+//      (X += u_{k+1} B_d'), which no longer wait for the state,
+//   3. rounds the states to BF16 into the state operand and signals "state
+//      written": the issuer adds the state MMAs (X += x_{k+1} D') behind them,
+//   4. accumulates the stage cost (x_{k+1}-g)' Q (x_{k+1}-g) from registers
+//      while those MMAs run.
+// So a step's critical path is the product itself plus one TMEM read and one
+// BF16 write-back; the stage cost and the inputs overlap the tensor core.
+// The input cost sum_k u_k' R u_k is added in closed form from the knots
+// (Gram of the knot weights), in FP32.
 //
 // Precision: D, B_d, x and u enter the product as BF16 (relative rounding
 // 2^-9); the accumulation onto the state and the cost stay FP32.  Every
 // mbarrier wait is bounded: past the limit the kernel sets status bit 2,
-// leaves the step loop, waits (bounded) for its MMAs in flight, frees its
-// tensor memory and returns.
+// every thread leaves the step loop, the issuer waits (bounded) for its MMAs
+// in flight, the tensor memory is freed and the kernel returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -40,13 +49,26 @@ constexpr int kKu = 64;          // K columns for the input (m padded)
 constexpr int kK = kKx + kKu;    // 192
 constexpr int kAtomBytes = 128 * 128;  // one 64-column swizzle atom of 128 rows
 constexpr int kOperandBytes = 3 * kAtomBytes;  // 128 rows x 192 BF16
-constexpr uint32_t kTmemCols = 128;    // the state (accumulator)
-constexpr long long kWaitPolls = 1ll << 26;
-constexpr int kChunks = 4;                     // state column chunks, one MMA group each
+constexpr uint32_t kWaitPolls = 1u << 26;
+constexpr int kChunks = 4;                     // state column chunks
 constexpr int kCW = kKx / kChunks;             // 32 states per chunk
 constexpr int kUW = kKu / kChunks;             // 16 inputs per chunk
-constexpr int kThreads = kChunks * kTileCands; // thread = (chunk, candidate row)
+constexpr int kEpiThreads = kChunks * kTileCands;  // thread = (chunk, candidate row)
+constexpr int kEpiWarps = kEpiThreads / 32;        // 16
+constexpr int kThreads = kEpiThreads + 32;         // + the issuing warp
 static_assert(kCW == 32, "one 32x32b.x32 TMEM access per thread and step");
+
+// Tensor-memory columns (32-bit): the FP32 state, then the BF16 A operand
+// (two values per column): the state part, and the input part twice; then
+// each thread's knots of the current segment (FP32), parked there so that the
+// epilogue threads' registers hold only the state.
+constexpr uint32_t kColX = 0;                  // [0, 128)   X, FP32
+constexpr uint32_t kColAx = kKx;               // [128, 192) bf16(x), 64 columns
+constexpr uint32_t kColAu = kColAx + kKx / 2;  // [192, 256) bf16(u), 2 x 32 columns
+constexpr uint32_t kAuCols = kKu / 2;
+constexpr uint32_t kColKnots = kColAu + 2 * kAuCols;  // [256, 384) U_a, U_b per chunk
+constexpr uint32_t kTmemCols = 512;
+static_assert(kColKnots + kChunks * 2 * kUW <= kTmemCols, "tensor-memory layout");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -72,33 +94,54 @@ __device__ __forceinline__ uint32_t idesc_bf16(uint32_t n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (tensor memory) += A (tensor memory, M x 16) * B (shared memory, 16 x N).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bd,
+                                            uint32_t idesc) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 1, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bd), "r"(idesc));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
         : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long it = 0; it < kWaitPolls; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// The CTA's abort flag (a shared int, by its shared-memory address).
+__device__ __forceinline__ int abort_get(uint32_t flag) {
+    int v;
+    asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(flag) : "memory");
+    return v;
+}
+__device__ __forceinline__ void abort_set(uint32_t flag) {
+    asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(flag), "r"(1) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up (and
+// then sets the abort flag) or another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t flag) {
+    for (uint32_t it = 0; it < kWaitPolls; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 255 && abort_get(flag)) return false;
     }
+    abort_set(flag);
     return false;
 }
 
@@ -137,10 +180,44 @@ __device__ __forceinline__ void tmem_st32(uint32_t addr, const float (&v)[32]) {
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};" ::"r"(addr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t addr, const uint32_t (&v)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ float4 lds4(uint32_t saddr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(saddr));
+    return v;
+}
+
 // Paired FP32 add and multiply (round to nearest, sm_100 and later).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// Two values rounded to BF16 in one 32-bit word, the first in the low half
+// (the lower K index, as in a K-major operand row).
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -160,24 +237,25 @@ __device__ __forceinline__ void put8(uint8_t* op, int r, int k, const float* v) 
 // those rows of U_i' W y_i, y_i,a = (R U_a)_i (the knots read from the
 // population, coherent with the breeding kernel before this one).  R is
 // symmetric, so row l of R gives column l's weights for every own row.
+template <int W>
 __device__ __forceinline__ float input_cost_dense_rows(const RolloutArgs& a, int cand, int i0,
                                                        int i1) {
     const int p = a.p, m = a.m;
-    float y[kUW], yp[kUW], up[kUW];
+    float y[W], yp[W], up[W];
 #pragma unroll
-    for (int r = 0; r < kUW; ++r) yp[r] = up[r] = 0.0f;
+    for (int r = 0; r < W; ++r) yp[r] = up[r] = 0.0f;
     float s = 0.0f;
     for (int j = 0; j < p; ++j) {
 #pragma unroll
-        for (int r = 0; r < kUW; ++r) y[r] = 0.0f;
+        for (int r = 0; r < W; ++r) y[r] = 0.0f;
         for (int l = 0; l < m; ++l) {
             const float ul = __ldcg(a.pop_in + (size_t)(l * p + j) * a.P + cand);
 #pragma unroll
-            for (int r = 0; r < kUW; ++r)
+            for (int r = 0; r < W; ++r)
                 if (i0 + r < i1) y[r] = fmaf(a.rmat[l * m + i0 + r], ul, y[r]);
         }
 #pragma unroll
-        for (int r = 0; r < kUW; ++r) {
+        for (int r = 0; r < W; ++r) {
             if (i0 + r >= i1) continue;
             const float u = __ldcg(a.pop_in + (size_t)((i0 + r) * p + j) * a.P + cand);
             s = fmaf(a.gram[j] * u, y[r], s);
@@ -190,41 +268,36 @@ __device__ __forceinline__ float input_cost_dense_rows(const RolloutArgs& a, int
 }
 
 struct Bf16Layout {
-    static constexpr int kA0 = 0;                      // A buffer 0
-    static constexpr int kA1 = kOperandBytes;          // A buffer 1
-    static constexpr int kB = 2 * kOperandBytes;       // B = [D | B_d]
-    static constexpr int kG = 3 * kOperandBytes;       // goal [128] f32
+    static constexpr int kB = 0;                       // B = [D | B_d], rows = states
+    static constexpr int kG = kOperandBytes;           // goal [128] f32
     static constexpr int kQ = kG + 128 * 4;            // diag Q [128] f32
     static constexpr int kKnots = kQ + 128 * 4;        // KnotStep[T]
-    __host__ __device__ static int par(int T) { return kKnots + 16 * T; }  // int[2*128]
-    __host__ __device__ static int part(int T) { return par(T) + 8 * kTileCands; }  // f32[4][128]
+    __host__ __device__ static int part(int T) { return kKnots + 16 * T; }  // f32[4][128]
     __host__ __device__ static int total(int T) {
         return part(T) + 4 * kChunks * kTileCands + 1024;
     }
 };
 
-// NG: the product issued as NG MMA groups of N = 128 / NG, each committed
-// to its own mbarrier (the autotuner picks NG).
-template <int NG>
 __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const RolloutArgs a) {
-    static_assert(NG == 1 || NG == 2 || NG == 4, "MMA groups");
-    constexpr int kGW = kKx / NG;  // columns (states) per MMA group
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint8_t* sA[2] = {sm + Bf16Layout::kA0, sm + Bf16Layout::kA1};
     uint8_t* sB = sm + Bf16Layout::kB;
     float* sg = reinterpret_cast<float*>(sm + Bf16Layout::kG);
     float* sq = reinterpret_cast<float*>(sm + Bf16Layout::kQ);
     KnotStep* ks = reinterpret_cast<KnotStep*>(sm + Bf16Layout::kKnots);
-    int* par = reinterpret_cast<int*>(sm + Bf16Layout::par(a.T));
     float* spart = reinterpret_cast<float*>(sm + Bf16Layout::part(a.T));
-    __shared__ __align__(8) uint64_t mbar[kChunks];
+    // bar_in: X read and u_{k+1} written (16 warp arrivals); bar_x: bf16(x_{k+1})
+    // written (16); bar_mma: the step's MMAs completed (one commit)
+    __shared__ __align__(8) uint64_t bar_in, bar_x, bar_mma;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
+    const uint32_t abort_f = smem_u32(&abort_sh);
+    const uint32_t b_in = smem_u32(&bar_in), b_x = smem_u32(&bar_x), b_mma = smem_u32(&bar_mma);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool issuer_warp = warp == kEpiWarps;
     const int q = warp >> 2;                         // state chunk / input chunk of this thread
-    const int row = ((warp & 3) << 5) | (tid & 31);  // candidate row = TMEM lane
+    const int row = ((warp & 3) << 5) | lane;        // candidate row = TMEM lane
     const int n = a.n, m = a.m, p = a.p, T = a.T;
     const int c0 = a.cand_begin + blockIdx.x * kTileCands;
     const int cand = c0 + row;
@@ -258,162 +331,208 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-#pragma unroll
-        for (int g = 0; g < NG; ++g)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[g])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_in)),
+                     "r"(kEpiWarps));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_x)),
+                     "r"(kEpiWarps));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma)));
         abort_sh = 0;
     }
+    // B was written by ordinary stores and is read by the MMAs (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 
     // ---- the knots (bred by the previous kernel) are read only after it completed
     pdl_wait_primary();
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // TMEM base published
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();  // TMEM base, barriers and operand B published
+    tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
-    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const float* src = a.pop_in;
-    const bool live = cand < a.P;
+    float jown = 0.0f;
+    int last_commit = -1;  // issuer: last step whose MMAs were committed
 
-    // ---- initial state: FP32 into this thread's chunk of its TMEM lane, BF16 into A[0]
-    {
-        float x0[kCW];
+    if (issuer_warp) {
+        // ---- the MMA issuer: step k = inputs u_k (after X was read), then the
+        // state x_k (after its BF16 copy was written), one commit per step
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kKx);
+            const uint64_t bd0 = sdesc(smem_u32(sB));
+            for (int k = 0; k < T; ++k) {
+                if (!mbar_wait(b_in, (uint32_t)(k & 1), abort_f)) break;
+                tc_fence_after();
+                const uint32_t au = tmem + kColAu + (uint32_t)(k & 1) * kAuCols;
 #pragma unroll
-        for (int j = 0; j < kCW; ++j) {
-            const int i = q * kCW + j;
-            x0[j] = i < n ? a.x0[i] : 0.0f;
-        }
-        tmem_st32(lane_base + q * kCW, x0);
-#pragma unroll
-        for (int j = 0; j < kCW; j += 8) put8(sA[0], row, q * kCW + j, x0 + j);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    // knots of the current segment (this thread's chunk of the inputs)
-    float ua[kUW], ub[kUW];
-    const int i0 = q * kUW;
-    int seg = -1;
-    float Ju = 0.0f;  // input cost of own inputs, closed form, accumulated per segment
-    auto load_segment = [&](int s) {
-#pragma unroll
-        for (int j = 0; j < kUW; ++j) {
-            const int i = i0 + j;
-            ua[j] = (live && i < m) ? __ldcg(src + (size_t)(i * p + s) * a.P + cand) : 0.0f;
-            ub[j] = (live && i < m && s + 1 < p) ? __ldcg(src + (size_t)(i * p + s + 1) * a.P + cand)
-                                                  : 0.0f;
-        }
-        // segments come in order, each once: W_ss U_s^2 + 2 W_s,s+1 U_s U_s+1,
-        // plus W_{p-1,p-1} U_{p-1}^2 with the last segment (diagonal R; a dense
-        // R is taken after the horizon loop)
-        if (a.rmat) return;
-        const float wd = a.gram[s];
-        const float wo = s + 1 < p ? 2.0f * a.gram[p + s] : 0.0f;
-        const float wl = s + 2 == p ? a.gram[s + 1] : 0.0f;
-#pragma unroll
-        for (int j = 0; j < kUW; ++j) {
-            if (i0 + j < m) {
-                float t = wd * ua[j] * ua[j];
-                t = fmaf(wo * ua[j], ub[j], t);
-                t = fmaf(wl * ub[j], ub[j], t);
-                Ju = fmaf(a.rdiag[i0 + j], t, Ju);
-            }
-        }
-    };
-    auto write_input = [&](uint8_t* op, const KnotStep& st) {
-        if (st.idx1 != seg) {
-            seg = st.idx1;
-            load_segment(seg);
-        }
-#pragma unroll
-        for (int j = 0; j < kUW; j += 8) {
-            float v[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = fmaf(st.w1, ub[j + e], st.w0 * ua[j + e]);
-            put8(op, row, kKx + i0 + j, v);
-        }
-    };
-    write_input(sA[0], ks[0]);
-
-    float2 jacc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                      make_float2(0.f, 0.f)};
-    bool ok = true;
-    int issued = -1;  // last step whose MMAs the issuing thread committed
-    const float4* g4 = reinterpret_cast<const float4*>(sg + q * kCW);
-    const float4* q4 = reinterpret_cast<const float4*>(sq + q * kCW);
-    auto stage_cost = [&](const float (&x)[kCW]) {
-#pragma unroll
-        for (int j = 0; j < kCW; j += 4) {
-            const float4 gg = g4[j / 4], qq = q4[j / 4];
-            const float2 e01 = add2(make_float2(x[j], x[j + 1]), make_float2(-gg.x, -gg.y));
-            const float2 e23 = add2(make_float2(x[j + 2], x[j + 3]), make_float2(-gg.z, -gg.w));
-            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[(j / 4) & 3]);
-            jacc[(j / 4) & 3] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[(j / 4) & 3]);
-        }
-    };
-    const uint32_t idesc = idesc_bf16(kGW);
-    const int grp = q * NG / kChunks;  // the MMA group holding this thread's chunk
-    for (int k = 0; k < T; ++k) {
-        uint8_t* Acur = sA[k & 1];
-        uint8_t* Anext = sA[(k + 1) & 1];
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (!__syncthreads_and(ok)) break;  // every thread leaves together
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // descriptors advance by (byte offset >> 4) in their start-address field;
-            // group g uses rows g*kGW .. of B (rows of 128 B within each atom)
-            const uint64_t ad0 = sdesc(smem_u32(Acur)), bd0 = sdesc(smem_u32(sB));
-#pragma unroll
-            for (int g = 0; g < NG; ++g) {
-#pragma unroll
-                for (int kk = 0; kk < kK / 16; ++kk) {
+                for (int jj = 0; jj < kKu / 16; ++jj) {
+                    const int kk = kKx / 16 + jj;  // K slice of B_d within B
                     const uint32_t off = ((kk >> 2) * kAtomBytes + (kk & 3) * 32) >> 4;
-                    mma_bf16(tmem + g * kGW, ad0 + off, bd0 + off + ((g * kGW * 128) >> 4),
-                             idesc, 1u);
+                    mma_bf16_ts(tmem + kColX, au + 8 * jj, bd0 + off, idesc);
                 }
-                mma_commit(&mbar[g]);
+                if (!mbar_wait(b_x, (uint32_t)(k & 1), abort_f)) {
+                    mma_commit(b_mma);  // track the input MMAs already issued
+                    last_commit = k;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < kKx / 16; ++kk) {
+                    const uint32_t off = ((kk >> 2) * kAtomBytes + (kk & 3) * 32) >> 4;
+                    mma_bf16_ts(tmem + kColX, tmem + kColAx + 8 * kk, bd0 + off, idesc);
+                }
+                mma_commit(b_mma);
+                last_commit = k;
             }
-            issued = k;
+            // MMAs still in flight are waited for (bounded) before the
+            // tensor memory is freed
+            if (last_commit >= 0) {
+                bool done = false;
+                for (uint32_t it = 0; it < kWaitPolls && !done; ++it)
+                    done = mbar_try(b_mma, (uint32_t)(last_commit & 1));
+                if (!done) abort_set(abort_f);
+            }
         }
-        // off the critical path: this thread's inputs of u_{k+1}, while the MMAs
-        // run (Anext was last read by the previous step's MMAs, which have completed)
-        if (k + 1 < T) write_input(Anext, ks[k + 1]);
-        if (!mbar_wait(&mbar[grp], (uint32_t)(k & 1))) {
-            ok = false;
-            continue;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float x[kCW];
-        tmem_ld32(lane_base + q * kCW, x);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        stage_cost(x);
-        if (k + 1 < T) {
+        __syncwarp();
+    } else {
+        // ---- epilogue threads: (chunk q, candidate row)
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const float* src = a.pop_in;
+        const bool live = cand < a.P;
+        const uint32_t knot_cols = lane_base + kColKnots + (uint32_t)(q * 2 * kUW);
+        const int i0 = q * kUW;
+        int seg = -1;
+        float Ju = 0.0f;  // input cost of own inputs, closed form, accumulated per segment
+        // U_s and U_s+1 of this thread's inputs into its knot columns
+        auto load_segment = [&](int s) {
+            float u[2 * kUW];  // [0, 16) = U_s, [16, 32) = U_s+1
 #pragma unroll
-            for (int j = 0; j < kCW; j += 8) put8(Anext, row, q * kCW + j, x + j);
+            for (int j = 0; j < kUW; ++j) {
+                const int i = i0 + j;
+                u[j] = (live && i < m) ? __ldcg(src + (size_t)(i * p + s) * a.P + cand) : 0.0f;
+                u[kUW + j] = (live && i < m && s + 1 < p)
+                                 ? __ldcg(src + (size_t)(i * p + s + 1) * a.P + cand)
+                                 : 0.0f;
+            }
+            tmem_st32(knot_cols, u);
+            // segments come in order, each once (knots <= horizon): W_ss U_s^2 +
+            // 2 W_s,s+1 U_s U_s+1, plus W_{p-1,p-1} U_{p-1}^2 with the last segment
+            // (diagonal R; a dense R is taken after the horizon loop)
+            if (!a.rmat) {
+                const float wd = a.gram[s];
+                const float wo = s + 1 < p ? 2.0f * a.gram[p + s] : 0.0f;
+                const float wl = s + 2 == p ? a.gram[s + 1] : 0.0f;
+#pragma unroll
+                for (int j = 0; j < kUW; ++j) {
+                    if (i0 + j < m) {
+                        const float ua = u[j], ub = u[kUW + j];
+                        float t = wd * ua * ua;
+                        t = fmaf(wo * ua, ub, t);
+                        t = fmaf(wl * ub, ub, t);
+                        Ju = fmaf(a.rdiag[i0 + j], t, Ju);
+                    }
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        };
+        // this thread's 16 inputs of u_k, BF16, into input buffer `buf`
+        auto write_input = [&](int buf, const KnotStep& st) {
+            if (st.idx1 != seg) {
+                seg = st.idx1;
+                load_segment(seg);
+            }
+            float u[2 * kUW];
+            tmem_ld32(knot_cols, u);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            uint32_t w[kUW / 2];
+#pragma unroll
+            for (int j = 0; j < kUW / 2; ++j)
+                w[j] = pack_bf16(fmaf(st.w1, u[kUW + 2 * j], st.w0 * u[2 * j]),
+                                 fmaf(st.w1, u[kUW + 2 * j + 1], st.w0 * u[2 * j + 1]));
+            tmem_st8(lane_base + kColAu + (uint32_t)buf * kAuCols + (uint32_t)(q * kUW / 2), w);
+        };
+        auto write_state = [&](const float (&x)[kCW]) {
+            uint32_t w[kCW / 2];
+#pragma unroll
+            for (int j = 0; j < kCW / 2; ++j) w[j] = pack_bf16(x[2 * j], x[2 * j + 1]);
+            tmem_st16(lane_base + kColAx + (uint32_t)(q * kCW / 2), w);
+        };
+        // publish this warp's tensor-memory stores to the issuer
+        auto signal = [&](uint32_t bar) {
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar);
+        };
+
+        // initial state: FP32 into X, BF16 into the state operand, u_0
+        {
+            float x0[kCW];
+#pragma unroll
+            for (int j = 0; j < kCW; ++j) {
+                const int i = q * kCW + j;
+                x0[j] = i < n ? a.x0[i] : 0.0f;
+            }
+            tmem_st32(lane_base + kColX + q * kCW, x0);
+            write_state(x0);
+            write_input(0, ks[0]);
+            signal(b_in);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_x);
         }
+
+        float2 jacc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        const uint32_t g_s = smem_u32(sg + q * kCW), q_s = smem_u32(sq + q * kCW);
+        auto stage_cost = [&](const float (&x)[kCW]) {
+#pragma unroll
+            for (int j = 0; j < kCW; j += 4) {
+                // goal and weights re-read every step (volatile: not hoisted
+                // into 64 registers across the loop)
+                const float4 gg = lds4(g_s + 4 * j), qq = lds4(q_s + 4 * j);
+                const float2 e01 = add2(make_float2(x[j], x[j + 1]), make_float2(-gg.x, -gg.y));
+                const float2 e23 =
+                    add2(make_float2(x[j + 2], x[j + 3]), make_float2(-gg.z, -gg.w));
+                jacc[0] = fma2(mul2(make_float2(qq.x, qq.y), e01), e01, jacc[0]);
+                jacc[1] = fma2(mul2(make_float2(qq.z, qq.w), e23), e23, jacc[1]);
+            }
+            // the sums are complete here: the next step's TMEM accesses (asm
+            // volatile, kept in order) cannot overlap the state's registers
+            asm volatile("" : "+f"(jacc[0].x), "+f"(jacc[0].y), "+f"(jacc[1].x), "+f"(jacc[1].y));
+        };
+        for (int k = 0; k < T; ++k) {
+            // inputs of step k+1 into the buffer step k-1's MMAs read (completed)
+            if (k + 1 < T) write_input((k + 1) & 1, ks[k + 1]);
+            if (!mbar_wait(b_mma, (uint32_t)(k & 1), abort_f)) break;
+            tc_fence_after();
+            float x[kCW];
+            tmem_ld32(lane_base + kColX + q * kCW, x);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (k + 1 < T) {
+                signal(b_in);  // X read, u_{k+1} written: the input MMAs may start
+                write_state(x);
+                signal(b_x);   // bf16(x_{k+1}) written: the state MMAs may start
+            }
+            stage_cost(x);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        if (a.rmat && live) {
+            // two halves of 8 rows keep the register count down
+            const int i1 = min(i0 + kUW, m), im = min(i0 + kUW / 2, i1);
+            Ju = input_cost_dense_rows<kUW / 2>(a, cand, i0, im) +
+                 input_cost_dense_rows<kUW / 2>(a, cand, im, i1);
+        }
+        jown = Ju;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) jown += jacc[j].x + jacc[j].y;
+        spart[q * kTileCands + row] = jown;
     }
-    // an abandoned step may still have MMAs in flight: wait (bounded) for them
-    // before the tensor memory is freed
-    if (tid == 0 && issued >= 0) {
-#pragma unroll
-        for (int g = 0; g < NG; ++g)
-            if (!mbar_wait(&mbar[g], (uint32_t)(issued & 1))) ok = false;
-    }
-    if (!ok) abort_sh = 1;
-    if (a.rmat && live) Ju = input_cost_dense_rows(a, cand, i0, min(i0 + kUW, m));
-    float jown = Ju;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) jown += jacc[j].x + jacc[j].y;
-    spart[q * kTileCands + row] = jown;
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    if (abort_sh) {
+    if (abort_get(abort_f)) {
         if (tid == 0 && a.status) atomicOr(a.status, 2);
-    } else if (live && q == 0) {
+    } else if (!issuer_warp && q == 0 && cand < a.P) {
         float J = spart[row];
 #pragma unroll
         for (int c = 1; c < kChunks; ++c) J += spart[c * kTileCands + row];
         a.cost[cand] = finite_or_inf(J);
     }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTmemCols));
@@ -429,26 +548,16 @@ bool rollout_bf16_supported(int n, int m, int T) {
     return n <= kKx && m <= kKu && rollout_bf16_smem_bytes(T) <= 227u * 1024u;
 }
 
-template <int NG>
-cudaError_t launch_groups(const RolloutArgs& a, cudaStream_t st) {
-    auto kern = rollout_bf16_kernel<NG>;
+cudaError_t launch_rollout_bf16(const RolloutArgs& a, cudaStream_t st) {
+    if (!rollout_bf16_supported(a.n, a.m, a.T)) return cudaErrorInvalidConfiguration;
+    if (a.mode != kEval) return cudaErrorInvalidValue;  // breeding runs in breed_kernel
+    auto kern = rollout_bf16_kernel;
     const size_t smem = rollout_bf16_smem_bytes(a.T);
     static int smem_cap[kMaxDevices] = {};
     if (cudaError_t e = raise_smem_limit(kern, smem, smem_cap); e != cudaSuccess) return e;
     const int grid = (a.P - a.cand_begin + kTileCands - 1) / kTileCands;
     if (grid <= 0) return cudaSuccess;
     return launch_kernel(kern, dim3(grid), dim3(kThreads), smem, st, a.pdl != 0, a);
-}
-
-cudaError_t launch_rollout_bf16(const RolloutArgs& a, int groups, cudaStream_t st) {
-    if (!rollout_bf16_supported(a.n, a.m, a.T)) return cudaErrorInvalidConfiguration;
-    if (a.mode != kEval) return cudaErrorInvalidValue;  // breeding runs in breed_kernel
-    switch (groups) {
-        case 1: return launch_groups<1>(a, st);
-        case 2: return launch_groups<2>(a, st);
-        case 4: return launch_groups<4>(a, st);
-        default: return cudaErrorInvalidConfiguration;
-    }
 }
 
 }  // namespace empc

@@ -221,7 +221,7 @@ bool rollout_shape_supported(const TileShape& s, int n, int m, int p, int T) {
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, const TileShape& s, cudaStream_t st) {
-    if (s.kind == 2) return launch_rollout_bf16(a, s.groups, st);
+    if (s.kind == 2) return launch_rollout_bf16(a, st);
     if (s.nx != compiled_nx(a.n)) return cudaErrorInvalidConfiguration;
     return s.kind == 1 ? launch_rollout_warp(a, s, st) : launch_rollout_block(a, s, st);
 }

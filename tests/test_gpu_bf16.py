@@ -34,6 +34,8 @@ def _eval(prob, x0, g, pop_np):
     dict(dof=64, radius=3, dt=0.005, T=60, p=8, P=300, E=16, q_pos=10.0, q_vel=1.0, r=1e-4),
     dict(dof=4, T=30, p=4, P=200, E=8),
     dict(dof=40, radius=3, dt=0.005, T=25, p=3, P=129, E=8),
+    # one knot: a constant input
+    dict(dof=6, T=17, p=1, P=130, E=8),
 ])
 def test_bf16_costs_against_oracle(kw):
     import paper_2001_04931_gb300 as E

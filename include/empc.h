@@ -156,6 +156,19 @@ empc_status empc_set_sigma(empc_handle h, float sigma);
  */
 empc_status empc_set_disturbance(empc_handle h, const double* w_d);
 
+/*
+ * empc_inject_stall - failure injection for tests of the BF16 tensor-core
+ * rollout (no counterpart in the paper).  From the next launch on, its MMA
+ * issuer stops at horizon step `step` (-1: never), so the other threads'
+ * waits run out; every wait of that kernel is limited to timeout_s seconds
+ * (one second until this is called).  A solve that hits the stall returns
+ * EMPC_ETIMEOUT and the context stays usable: call again with step -1 and
+ * solve (empc_reset first for a fresh population).  Synchronous.
+ * EMPC_EUNSUPPORTED unless the handle's precision is EMPC_BF16; EMPC_EINVAL
+ * for step < -1 or timeout_s outside (0, 60].
+ */
+empc_status empc_inject_stall(empc_handle h, int step, double timeout_s);
+
 /* Flags of empc_set_state_box. */
 enum { EMPC_BOX_CLAMP = 1, EMPC_BOX_PENALTY = 2 };
 

@@ -110,6 +110,7 @@ _SIGNATURES = {
     "empc_batch_get_state": (_i, [_h, _i, _vp, _vp, _vp]),
     "empc_batch_get_info": (_i, [_h, ctypes.POINTER(empc_batch_info)]),
     "empc_batch_inject_stall": (_i, [_h, _i, ctypes.c_double]),
+    "empc_inject_stall": (_i, [_h, _i, ctypes.c_double]),
     "empc_batch_destroy": (None, [_h]),
     "empc_batch_last_error": (ctypes.c_char_p, [_h]),
 }
@@ -349,6 +350,11 @@ class Problem:
 
     def set_stream(self, stream):
         check(_lib.empc_set_stream(self.handle, stream), self.handle)
+
+    def inject_stall(self, step, timeout_s):
+        """Test hook (BF16 handles): the tensor-core rollout's MMA issuer stops
+        at horizon step `step` (-1: never); its waits run out after timeout_s."""
+        check(_lib.empc_inject_stall(self.handle, int(step), float(timeout_s)), self.handle)
 
 
 _COST_FN = None

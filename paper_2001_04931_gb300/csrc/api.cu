@@ -81,6 +81,8 @@ struct empc_problem_s {
     int refine_cands = 1, refine_wpc = 2;  // adjoint shape for the elites' refinement
     int grad_nx = 0;  // the adjoint kernel's state class (the warp family's, n <= 64)
     float* sigma_dev = nullptr;  // the mutation sigma the breeding kernel reads
+    int* inject = nullptr;       // tensor-core rollout: [stall step, wait limit us]
+    int inject_h[2] = {-1, 1000000};  // host copy being transferred to inject
     float sigma_now = 0.0f;      // host copy being transferred to sigma_dev
     // state-box hook: [3][n] lo, hi, rho on the device and its host copy
     float* box = nullptr;
@@ -154,6 +156,7 @@ RolloutArgs base_args(empc_handle h) {
     a.pm256 = h->cfg.p_mutate_256;
     a.gate = h->cfg.gate;
     a.status = h->status;
+    a.inject = h->inject;
     return a;
 }
 
@@ -570,7 +573,7 @@ void free_handle(empc_handle h) {
     void* bufs[] = {h->D_, h->BT, h->qdiag, h->rdiag, h->gram, h->umin, h->umax, h->x0,
                     h->goal, h->ktab, h->pop[0], h->pop[1], h->cost, h->elite_idx,
                     h->elite_cost, h->best_knots, h->best_cost, h->gen, h->status,
-                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev, h->box,
+                    h->Hc, h->gvec, h->c0, h->zero_knots, h->sigma_dev, h->inject, h->box,
                     h->wd_dev, h->rmat, h->Vt_dev, h->ev_x0, h->ev_goal};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -809,6 +812,7 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(dev_alloc(&h->gen, 1));
     EMPC_TRY(dev_alloc(&h->status, 1));
     EMPC_TRY(dev_alloc(&h->sigma_dev, 1));
+    EMPC_TRY(dev_alloc(&h->inject, 2));
     if (tb.dense_r) EMPC_TRY(dev_alloc(&h->rmat, tb.rmat.size()));
     h->rotated = tb.rotated;
     if (tb.rotated) {
@@ -833,6 +837,7 @@ empc_status empc_create(const double* A, const double* B, const double* Q, const
     EMPC_TRY(cudaMemsetAsync(h->gen, 0, sizeof(uint32_t), st));
     EMPC_TRY(cudaMemsetAsync(h->status, 0, sizeof(int), st));
     EMPC_TRY(cudaMemcpyAsync(h->sigma_dev, &h->cfg.sigma, sizeof(float), cudaMemcpyHostToDevice, st));
+    EMPC_TRY(cudaMemcpyAsync(h->inject, h->inject_h, sizeof(h->inject_h), cudaMemcpyHostToDevice, st));
     if (tb.dense_r)
         EMPC_TRY(cudaMemcpyAsync(h->rmat, tb.rmat.data(), sizeof(float) * tb.rmat.size(),
                                  cudaMemcpyHostToDevice, st));
@@ -915,6 +920,21 @@ empc_status empc_set_sigma(empc_handle h, float sigma) {
     h->sigma_now = sigma;
     EMPC_CUDA(h, cudaMemcpyAsync(h->sigma_dev, &h->sigma_now, sizeof(float),
                                  cudaMemcpyHostToDevice, h->stream));
+    return EMPC_OK;
+}
+
+empc_status empc_inject_stall(empc_handle h, int step, double timeout_s) {
+    if (!h) return fail(nullptr, EMPC_EINVAL, "NULL handle");
+    if (h->cfg.precision != EMPC_BF16)
+        return fail(h, EMPC_EUNSUPPORTED, "stall injection is for the BF16 tensor-core rollout");
+    if (step < -1 || !(timeout_s > 0.0) || !(timeout_s <= 60.0))
+        return fail(h, EMPC_EINVAL, "need step >= -1 and 0 < timeout_s <= 60");
+    EMPC_CUDA(h, cudaStreamSynchronize(h->stream));  // inject_h is not in use by a copy
+    h->inject_h[0] = step;
+    h->inject_h[1] = std::max(1, (int)std::lround(timeout_s * 1e6));
+    EMPC_CUDA(h, cudaMemcpyAsync(h->inject, h->inject_h, sizeof(h->inject_h),
+                                 cudaMemcpyHostToDevice, h->stream));
+    EMPC_CUDA(h, cudaStreamSynchronize(h->stream));
     return EMPC_OK;
 }
 

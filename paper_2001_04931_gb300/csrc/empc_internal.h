@@ -57,6 +57,10 @@ struct RolloutArgs {
     int cand_begin;  // first candidate this launch covers (later ones up to P)
     int pdl;         // launch with programmatic stream serialization
     int* status;     // bit 1 (value 2): a bounded device wait gave up (may be null)
+    // tensor-core rollout only, on the device or null: [0] the step at which
+    // the MMA issuer stops (a host-side stall injection; -1: none), [1] the
+    // limit of each of its waits in microseconds (null: one second)
+    const int* inject;
 };
 
 // Launch `kern` with an optional programmatic-stream-serialization attribute

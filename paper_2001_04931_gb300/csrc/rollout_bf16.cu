@@ -32,9 +32,12 @@
 //
 // Precision: D, B_d, x and u enter the product as BF16 (relative rounding
 // 2^-9); the accumulation onto the state and the cost stay FP32.  Every
-// mbarrier wait is bounded: past the limit the kernel sets status bit 2,
-// every thread leaves the step loop, the issuer waits (bounded) for its MMAs
-// in flight, the tensor memory is freed and the kernel returns.
+// mbarrier wait is bounded in time (one second unless the handle sets
+// another limit): past the limit the kernel sets status bit 2, every thread
+// leaves the step loop, the issuer waits (bounded) for its MMAs in flight,
+// the tensor memory is freed and the kernel returns.  A host-side injection
+// can make the issuer stop at a given step, so that the other threads' waits
+// run out (the test of that path).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -49,7 +52,8 @@ constexpr int kKu = 64;          // K columns for the input (m padded)
 constexpr int kK = kKx + kKu;    // 192
 constexpr int kAtomBytes = 128 * 128;  // one 64-column swizzle atom of 128 rows
 constexpr int kOperandBytes = 3 * kAtomBytes;  // 128 rows x 192 BF16
-constexpr uint32_t kWaitPolls = 1u << 26;
+constexpr uint32_t kWaitPolls = 1u << 26;  // the final wait for MMAs in flight
+constexpr uint32_t kDefaultWaitUs = 1000000u;
 constexpr int kChunks = 4;                     // state column chunks
 constexpr int kCW = kKx / kChunks;             // 32 states per chunk
 constexpr int kUW = kKu / kChunks;             // 16 inputs per chunk
@@ -134,12 +138,28 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return done != 0;
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if it gave up (and
-// then sets the abort flag) or another thread already gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t flag) {
-    for (uint32_t it = 0; it < kWaitPolls; ++it) {
+// %globaltimer in units of 1.024 us, 32 bits (wraps after 73 minutes; the
+// differences taken below are modular).
+__device__ __forceinline__ uint32_t global_us() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (uint32_t)(t >> 10);
+}
+
+// Wait for phase `parity` of an mbarrier, for at most about limit_us
+// microseconds; false if it gave up (and then sets the abort flag) or another
+// thread already gave up.  The clock and the flag are read every 256 polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t flag,
+                                          uint32_t limit_us) {
+    uint32_t t0 = 0;
+    for (uint32_t it = 0; it < (1u << 31); ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 255) == 255 && abort_get(flag)) return false;
+        if ((it & 255) == 255) {
+            if (abort_get(flag)) return false;
+            const uint32_t t = global_us();
+            if (it == 255) t0 = t;
+            else if (t - t0 > limit_us) break;
+        }
     }
     abort_set(flag);
     return false;
@@ -349,6 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
     const uint32_t tmem = tmem_base_sh;
     float jown = 0.0f;
     int last_commit = -1;  // issuer: last step whose MMAs were committed
+    const int stall_step = a.inject ? a.inject[0] : -1;
+    const uint32_t wait_us = a.inject ? (uint32_t)a.inject[1] : kDefaultWaitUs;
 
     if (issuer_warp) {
         // ---- the MMA issuer: step k = inputs u_k (after X was read), then the
@@ -357,7 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
             const uint32_t idesc = idesc_bf16(kKx);
             const uint64_t bd0 = sdesc(smem_u32(sB));
             for (int k = 0; k < T; ++k) {
-                if (!mbar_wait(b_in, (uint32_t)(k & 1), abort_f)) break;
+                if (k == stall_step) break;  // injected stall: the step is never issued
+                if (!mbar_wait(b_in, (uint32_t)(k & 1), abort_f, wait_us)) break;
                 tc_fence_after();
                 const uint32_t au = tmem + kColAu + (uint32_t)(k & 1) * kAuCols;
 #pragma unroll
@@ -366,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
                     const uint32_t off = ((kk >> 2) * kAtomBytes + (kk & 3) * 32) >> 4;
                     mma_bf16_ts(tmem + kColX, au + 8 * jj, bd0 + off, idesc);
                 }
-                if (!mbar_wait(b_x, (uint32_t)(k & 1), abort_f)) {
+                if (!mbar_wait(b_x, (uint32_t)(k & 1), abort_f, wait_us)) {
                     mma_commit(b_mma);  // track the input MMAs already issued
                     last_commit = k;
                     break;
@@ -498,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         for (int k = 0; k < T; ++k) {
             // inputs of step k+1 into the buffer step k-1's MMAs read (completed)
             if (k + 1 < T) write_input((k + 1) & 1, ks[k + 1]);
-            if (!mbar_wait(b_mma, (uint32_t)(k & 1), abort_f)) break;
+            if (!mbar_wait(b_mma, (uint32_t)(k & 1), abort_f, wait_us)) break;
             tc_fence_after();
             float x[kCW];
             tmem_ld32(lane_base + kColX + q * kCW, x);

@@ -90,6 +90,7 @@ def test_null_handle_calls_fail_cleanly(E):
     assert E.empc_solve(None, None, None, 1, None, None) == E.EMPC_EINVAL
     assert E.empc_set_state_box(None, None, None, None, E.EMPC_BOX_CLAMP) == E.EMPC_EINVAL
     assert E.empc_set_disturbance(None, None) == E.EMPC_EINVAL
+    assert E.empc_inject_stall(None, 3, 0.1) == E.EMPC_EINVAL
     assert b"NULL" in E.empc_last_error(None)
     E.empc_destroy(None)
 

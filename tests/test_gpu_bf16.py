@@ -131,3 +131,54 @@ def test_bf16_costs_c5_horizon_evolved_population():
     tE = np.sort(oc)[wl.E - 1]
     assert (oc[el] <= tE * (1 + 2 * C5_MAX_RTOL)).all()
     prob.close()
+
+
+def test_bf16_wait_runs_out_and_reports_timeout():
+    """Failure detection of the tensor-core rollout without a GPU fault: the
+    MMA issuer is made to stop at step 7 (host-side injection), so the other
+    threads' bounded waits run out after 50 ms; the solve reports
+    EMPC_ETIMEOUT, and after the injection is cleared the same handle solves
+    again with costs matching the oracle (the context stayed usable)."""
+    import time
+    import torch
+    import paper_2001_04931_gb300 as E
+    wl = W.small(dof=16, radius=3, dt=0.005, T=40, p=5, P=256, E=16)
+    prob = gpu_problem(wl, seed=5, precision=E.EMPC_BF16)
+    x0, g = wl.start_goal()
+    prob.inject_stall(7, 0.05)
+    t = time.perf_counter()
+    with pytest.raises(E.EmpcError) as ei:
+        prob.solve(x0, g, 1)
+    assert ei.value.status == E.EMPC_ETIMEOUT
+    assert time.perf_counter() - t < 30.0
+    prob.inject_stall(-1, 1.0)
+    prob.reset()
+    gen = prob.info().generation  # the counter moved on with the failed solve
+    prob.solve(x0, g, 1)
+    pop = torch.empty((prob.D, prob.P), device="cuda")
+    cost = torch.empty(prob.P, device="cuda")
+    prob.get_state(pop, cost, None)
+    torch.cuda.synchronize()
+    pop, cost = pop.cpu().numpy(), cost.cpu().numpy()
+    b = wl.bounds().astype(np.float32)
+    np.testing.assert_array_equal(
+        pop.view(np.uint32),
+        O.breed_cold(5, gen, b[:, 0], b[:, 1], wl.m, wl.p, wl.P).view(np.uint32))
+    assert rel_err(cost, oracle_model(wl).cost_population(x0, g, pop)).max() <= MAX_RTOL
+    prob.close()
+
+
+def test_inject_stall_is_for_bf16_handles():
+    import paper_2001_04931_gb300 as E
+    wl = W.small(dof=3, T=20, p=4, P=128, E=8)
+    prob = gpu_problem(wl)
+    with pytest.raises(E.EmpcError) as ei:
+        prob.inject_stall(3, 0.1)
+    assert ei.value.status == E.EMPC_EUNSUPPORTED
+    prob.close()
+    bf = gpu_problem(wl, precision=E.EMPC_BF16)
+    for step, t in ((-2, 0.1), (3, 0.0), (3, 61.0)):
+        with pytest.raises(E.EmpcError) as ei:
+            bf.inject_stall(step, t)
+        assert ei.value.status == E.EMPC_EINVAL
+    bf.close()

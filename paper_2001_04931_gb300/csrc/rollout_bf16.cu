@@ -16,8 +16,8 @@
 //
 // Roles.  One thread of a 17th warp issues every MMA.  The 512 threads of
 // the other 16 warps are (32-state chunk, candidate) pairs; per step each
-//   1. writes its 16 inputs of u_{k+1} (the segment's knots parked in tensor
-//      memory) into the spare input buffer while step k's MMAs run,
+//   1. writes its 16 inputs of u_{k+1} (the segment's knots kept in
+//      registers) into the spare input buffer while step k's MMAs run,
 //   2. waits for step k's MMAs, reads its 32 states of x_{k+1} from X, and
 //      signals "X read": the issuer starts step k+1 with the input MMAs
 //      (X += u_{k+1} B_d'), which no longer wait for the state,
@@ -63,16 +63,13 @@ constexpr int kThreads = kEpiThreads + 32;         // + the issuing warp
 static_assert(kCW == 32, "one 32x32b.x32 TMEM access per thread and step");
 
 // Tensor-memory columns (32-bit): the FP32 state, then the BF16 A operand
-// (two values per column): the state part, and the input part twice; then
-// each thread's knots of the current segment (FP32), parked there so that the
-// epilogue threads' registers hold only the state.
+// (two values per column): the state part, and the input part twice.
 constexpr uint32_t kColX = 0;                  // [0, 128)   X, FP32
 constexpr uint32_t kColAx = kKx;               // [128, 192) bf16(x), 64 columns
 constexpr uint32_t kColAu = kColAx + kKx / 2;  // [192, 256) bf16(u), 2 x 32 columns
 constexpr uint32_t kAuCols = kKu / 2;
-constexpr uint32_t kColKnots = kColAu + 2 * kAuCols;  // [256, 384) U_a, U_b per chunk
-constexpr uint32_t kTmemCols = 512;
-static_assert(kColKnots + kChunks * 2 * kUW <= kTmemCols, "tensor-memory layout");
+constexpr uint32_t kTmemCols = 256;
+static_assert(kColAu + 2 * kAuCols == kTmemCols, "tensor-memory layout");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -418,13 +415,12 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         const float* src = a.pop_in;
         const bool live = cand < a.P;
-        const uint32_t knot_cols = lane_base + kColKnots + (uint32_t)(q * 2 * kUW);
         const int i0 = q * kUW;
         int seg = -1;
         float Ju = 0.0f;  // input cost of own inputs, closed form, accumulated per segment
         // U_s and U_s+1 of this thread's inputs into its knot columns
+        float u[2 * kUW];  // [0, 16) = U_s, [16, 32) = U_s+1 of the current segment
         auto load_segment = [&](int s) {
-            float u[2 * kUW];  // [0, 16) = U_s, [16, 32) = U_s+1
 #pragma unroll
             for (int j = 0; j < kUW; ++j) {
                 const int i = i0 + j;
@@ -433,7 +429,6 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
                                  ? __ldcg(src + (size_t)(i * p + s + 1) * a.P + cand)
                                  : 0.0f;
             }
-            tmem_st32(knot_cols, u);
             // segments come in order, each once (knots <= horizon): W_ss U_s^2 +
             // 2 W_s,s+1 U_s U_s+1, plus W_{p-1,p-1} U_{p-1}^2 with the last segment
             // (diagonal R; a dense R is taken after the horizon loop)
@@ -452,7 +447,6 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
                     }
                 }
             }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         };
         // this thread's 16 inputs of u_k, BF16, into input buffer `buf`
         auto write_input = [&](int buf, const KnotStep& st) {
@@ -460,9 +454,6 @@ __global__ void __launch_bounds__(kThreads, 1) rollout_bf16_kernel(const Rollout
                 seg = st.idx1;
                 load_segment(seg);
             }
-            float u[2 * kUW];
-            tmem_ld32(knot_cols, u);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             uint32_t w[kUW / 2];
 #pragma unroll
             for (int j = 0; j < kUW / 2; ++j)

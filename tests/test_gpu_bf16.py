@@ -36,6 +36,8 @@ def _eval(prob, x0, g, pop_np):
     dict(dof=40, radius=3, dt=0.005, T=25, p=3, P=129, E=8),
     # one knot: a constant input
     dict(dof=6, T=17, p=1, P=130, E=8),
+    # a one-step horizon: one commit, no operand written for a next step
+    dict(dof=4, T=1, p=1, P=130, E=8),
 ])
 def test_bf16_costs_against_oracle(kw):
     import paper_2001_04931_gb300 as E
@@ -182,3 +184,20 @@ def test_inject_stall_is_for_bf16_handles():
             bf.inject_stall(step, t)
         assert ei.value.status == E.EMPC_EINVAL
     bf.close()
+
+
+def test_bf16_rejects_sizes_beyond_its_tile():
+    """The tensor-core tile holds n <= 128 states and m <= 64 inputs: a model
+    with m = 70 inputs (n = 100, within the library's FP32 limits) is refused
+    at create with BF16, not truncated, and accepted with FP32."""
+    import paper_2001_04931_gb300 as E
+    n, m = 100, 70
+    rng = np.random.default_rng(3)
+    A = np.eye(n) * 0.99
+    B = rng.uniform(-0.01, 0.01, (n, m))
+    Q, R = np.eye(n), 1e-3 * np.eye(m)
+    bounds = np.tile([-1.0, 1.0], (m, 1))
+    with pytest.raises(E.EmpcError) as ei:
+        E.Problem(A, B, Q, R, bounds, 10, 2, 128, elite=8, precision=E.EMPC_BF16)
+    assert ei.value.status == E.EMPC_EUNSUPPORTED
+    E.Problem(A, B, Q, R, bounds, 10, 2, 128, elite=8).close()

@@ -88,6 +88,16 @@ def test_lockstep_c1_full_size():
     _lockstep(W.config("c1"), 5)
 
 
+def test_lockstep_breeding_at_a_million_knot_groups():
+    """8192 candidates of 512 knots (the 64-DoF chain's knot count): 2^20
+    four-knot groups, one breeding thread each; the bred populations equal
+    the oracle's draws bit for bit (cold, then two warm generations)."""
+    wl = W.small(dof=64, radius=3, dt=0.005, T=8, p=8, P=8192, E=64, q_pos=10.0, q_vel=1.0,
+                 r=1e-4)
+    assert wl.P * (wl.m * wl.p // 4) == 1 << 20
+    _lockstep(wl, 3, seed=4, sample=np.arange(0, wl.P, 97))
+
+
 @pytest.mark.parametrize("gate", [0, 1, 2])
 def test_lockstep_gate_modes(gate):
     _lockstep(W.small(dof=2, T=17, p=3, P=96, E=8, sigma=0.3), 3, gate=gate)

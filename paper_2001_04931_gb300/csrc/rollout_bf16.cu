@@ -8,11 +8,11 @@
 //   X[c][i] += sum_{j<64} u_c[j] B_d[i][j] + sum_{k<128} x_c[k] D[i][k].
 // The FP32 state X lives in tensor memory for the whole horizon (TMEM lane =
 // candidate, column = state): the MMAs add the increment to it, so no thread
-// keeps or updates a master copy.  The A operand, [u_c | x_c] in BF16, lives
-// in tensor memory too (two BF16 per 32-bit column, lane = candidate), so the
-// MMAs read only the constant B = [B_d | D] (states x K, K-major, 128-byte
-// swizzle) from shared memory, and the epilogue writes its BF16 state with
-// tcgen05.st instead of shared-memory stores.
+// keeps or updates a master copy.  The A operands, bf16(x_c) and bf16(u_c),
+// live in tensor memory too (two BF16 per 32-bit column, lane = candidate),
+// so the MMAs read only the constant B = [D | B_d] (states x K, K-major,
+// 128-byte swizzle) from shared memory, and the epilogue writes its BF16
+// state with tcgen05.st instead of shared-memory stores.
 //
 // Roles.  One thread of a 17th warp issues every MMA.  The 512 threads of
 // the other 16 warps are (32-state chunk, candidate) pairs; per step each

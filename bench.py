@@ -412,7 +412,7 @@ def compact(line):
     """The figures of a workload's bench line that its variant record keeps."""
     roof = line["roofline"]
     keep = ("bound", "kernel", "achieved", "peak", "unit", "frac", "peak_basis", "launch_us",
-            "flops_per_launch", "epilogue_fp32")
+            "flops_per_launch", "mma_flops_per_launch", "traffic", "epilogue_fp32")
     out = {"workload": line["config"]["workload"], "dtype": line["dtype"],
            "metric": line["metric"], "value": line["value"], "unit": line["unit"],
            "steps": line["steps"], "warmup": line["warmup"],

@@ -38,6 +38,8 @@ def _eval(prob, x0, g, pop_np):
     dict(dof=6, T=17, p=1, P=130, E=8),
     # a one-step horizon: one commit, no operand written for a next step
     dict(dof=4, T=1, p=1, P=130, E=8),
+    # fewer candidates than one tile: most TMEM lanes hold no candidate
+    dict(dof=3, T=10, p=2, P=50, E=4),
 ])
 def test_bf16_costs_against_oracle(kw):
     import paper_2001_04931_gb300 as E

@@ -129,24 +129,15 @@ __device__ __forceinline__ void rank_words(unsigned long long* s, int L, Visit&&
         const unsigned long long x = s[e];
         const int ce = e >> 6;
         int rank = e & 63;
-        // four chunks searched side by side: their dependent loads overlap
-        for (int c0 = 0; c0 < C; c0 += 4) {
-            int pos[4] = {0, 0, 0, 0};
+        for (int c = 0; c < C; ++c) {
+            if (c == ce) continue;
+            const unsigned long long* ch = s + 64 * c;
+            int pos = 0;
 #pragma unroll
-            for (int step = 32; step > 0; step >>= 1) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int c = c0 + u;
-                    if (c < C && s[64 * c + pos[u] + step - 1] < x) pos[u] += step;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = c0 + u;
-                if (c >= C || c == ce) continue;
-                if (pos[u] == 63 && s[64 * c + 63] < x) pos[u] = 64;
-                rank += pos[u];
-            }
+            for (int step = 32; step > 0; step >>= 1)
+                if (ch[pos + step - 1] < x) pos += step;
+            if (pos == 63 && ch[63] < x) pos = 64;
+            rank += pos;
         }
         visit(rank, x);
     }

@@ -38,3 +38,22 @@ def test_record_file_names_its_sources():
 
 def test_whole_job_rate_counts_every_rank():
     assert bench.whole_job_rate(1000, 4, 2.0) == 2000.0
+
+
+def test_variant_record_keeps_the_roofline_evidence():
+    """A variant's record in the default line keeps what its roofline claim
+    rests on: the fraction, the kernel's time, its algorithmic work, the DRAM
+    traffic figure and, for the tensor-core rollout, the issued MMA work."""
+    roof = {"bound": "tensor", "kernel": "k", "achieved": 550.0, "peak": 1912.2, "unit": "TFLOP/s",
+            "frac": 0.29, "peak_basis": "measured", "launch_us": 194.0,
+            "flops_per_launch": 1.07e11, "mma_flops_per_launch": 1.61e11,
+            "traffic": 33712640, "breed_us": 65.0}
+    line = {"config": {"workload": "c5"}, "dtype": "bf16", "metric": bench.METRIC, "value": 1.0,
+            "unit": bench.UNIT, "steps": 1, "warmup": 3, "ms_per_step": 10.9,
+            "ms_per_problem": 10.9, "e2e": {}, "gpu_launches": 120, "clocks": {},
+            "roofline": roof, "compare": {"median_speedup": 14.9}}
+    out = bench.compact(line)
+    for k in ("frac", "launch_us", "flops_per_launch", "mma_flops_per_launch", "traffic"):
+        assert out["roofline"][k] == roof[k]
+    assert "breed_us" not in out["roofline"]
+    assert out["compare"] == line["compare"]

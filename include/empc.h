@@ -53,8 +53,9 @@ typedef enum {
  * the per-step product x_k D' + u_k B_d' on the tensor cores (tcgen05) with
  * BF16 operands, the state, the force and the cost accumulated in FP32; it
  * needs n <= 128 and m <= 64 and takes no refinement, disturbance or state
- * box; costs within about 1e-3 relative of the FP64 definition (measured
- * 1.5e-4 on a 64-DoF chain over 200 steps).  Its device waits are bounded in
+ * box; its costs differ from the FP64 definition by the BF16 rounding of
+ * the operands (measured: 1.5e-4 relative at most on a 64-DoF chain over 200
+ * steps, up to 2.6e-3 on small chains).  Its device waits are bounded in
  * time, one second unless empc_inject_stall sets another limit. */
 typedef enum { EMPC_FP32 = 0, EMPC_BF16 = 1 } empc_precision;
 
